@@ -1,0 +1,259 @@
+"""CPU oracle of the truncated SVD method of the svds-C paper (arXiv 2405.18966).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is a plain, slow FP64 C implementation
+(``svds_oracle.c``) of Alg. 1 (Lanczos bidiagonalization), the full
+re-orthogonalization of Sec. 2.1 (as two classical Gram-Schmidt passes), the
+residual test of Eq. (4) and the augmented restart of Eq. (5)-(7) / Alg. 2,
+plus a one-sided Jacobi dense SVD used for the projected matrix and as a
+brute-force checker.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+It shares no code with the CUDA solver and never imports it.
+
+Matrices are passed as any object with ``m, n, row_ptr, col_idx, values``
+(0-based CSR, int64 row pointers, int32 column indices) or ``m, n, a``
+(column-major float64), or as a 2-D numpy array (treated as dense).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "svds_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, strict FP64: no contraction into FMA)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Mat(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("m", C.c_int64), ("n", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("val", C.c_void_p),
+                ("a", C.c_void_p), ("lda", C.c_int64)]
+
+
+class Info(C.Structure):
+    _fields_ = [("converged", C.c_int32), ("nconv", C.c_int32), ("restarts", C.c_int32),
+                ("breakdowns", C.c_int32), ("n_matvec", C.c_int64), ("n_steps", C.c_int64),
+                ("svd_sweeps_max", C.c_int32), ("stopped_early", C.c_int32),
+                ("anorm_est", C.c_double), ("beta_t", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
+            L.orc_matvec.argtypes = [C.POINTER(_Mat), vp, vp]
+            L.orc_matvec_t.argtypes = [C.POINTER(_Mat), vp, vp]
+            L.orc_gemv_t.argtypes = [i64, i64, vp, i64, vp, vp]
+            L.orc_gemv_n_sub.argtypes = [i64, i64, vp, i64, vp, vp]
+            L.orc_cgs2.argtypes = [i64, i64, vp, i64, vp, vp]
+            L.orc_norm2.argtypes = [i64, vp]
+            L.orc_norm2.restype = dbl
+            L.orc_gemm_nn.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64]
+            L.orc_rng_normal.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+            L.orc_rng_normal.restype = dbl
+            L.orc_splitmix64.argtypes = [C.c_uint64]
+            L.orc_splitmix64.restype = C.c_uint64
+            L.orc_rng_vector.argtypes = [C.c_uint64, C.c_uint64, i64, vp]
+            L.orc_jacobi_svd.argtypes = [i64, i64, vp, i64, vp, vp, i64, vp, i64, C.c_int]
+            L.orc_jacobi_svd.restype = C.c_int
+            L.orc_sign_normalize.argtypes = [i64, i64, i64, vp, i64, vp, i64]
+            L.orc_svds.argtypes = [C.POINTER(_Mat), i64, i64, dbl, i64, C.c_uint64, vp, i64,
+                                   vp, vp, i64, vp, i64, vp, C.POINTER(Info), vp, vp, vp]
+            L.orc_svds.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_get_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class _Bound:
+    """Keeps the numpy arrays a _Mat points into alive."""
+
+    def __init__(self, A):
+        if isinstance(A, np.ndarray):
+            a = np.asfortranarray(A, dtype=np.float64)
+            self.keep = [a]
+            self.mat = _Mat(1, 0, a.shape[0], a.shape[1], None, None, None,
+                            a.ctypes.data, a.shape[0])
+        elif hasattr(A, "row_ptr"):
+            rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+            ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+            va = np.ascontiguousarray(A.values, dtype=np.float64)
+            self.keep = [rp, ci, va]
+            self.mat = _Mat(0, 0, int(A.m), int(A.n), rp.ctypes.data, ci.ctypes.data,
+                            va.ctypes.data, None, 0)
+        else:
+            a = np.asfortranarray(A.a, dtype=np.float64)
+            self.keep = [a]
+            self.mat = _Mat(1, 0, a.shape[0], a.shape[1], None, None, None,
+                            a.ctypes.data, a.shape[0])
+        self.m, self.n = int(self.mat.m), int(self.mat.n)
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def matvec(A, x):
+    """y = A x (Alg. 1 lines 2, 7)."""
+    b = _Bound(A)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(b.m)
+    lib().orc_matvec(C.byref(b.mat), _ptr(x), _ptr(y))
+    return y
+
+
+def matvec_t(A, x):
+    """y = A^T x (Alg. 1 line 5)."""
+    b = _Bound(A)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(b.n)
+    lib().orc_matvec_t(C.byref(b.mat), _ptr(x), _ptr(y))
+    return y
+
+
+def gemv_t(W, w):
+    W = np.asfortranarray(W, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    h = np.empty(W.shape[1])
+    lib().orc_gemv_t(W.shape[0], W.shape[1], _ptr(W), W.shape[0], _ptr(w), _ptr(h))
+    return h
+
+
+def gemv_n_sub(W, h, w):
+    """w - W h."""
+    W = np.asfortranarray(W, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    w = np.array(w, dtype=np.float64, copy=True)
+    lib().orc_gemv_n_sub(W.shape[0], W.shape[1], _ptr(W), W.shape[0], _ptr(h), _ptr(w))
+    return w
+
+
+def cgs2(W, w):
+    """(I - W W^T) applied twice to w (Sec. 2.1 full re-orthogonalization)."""
+    W = np.asfortranarray(W, dtype=np.float64)
+    w = np.array(w, dtype=np.float64, copy=True)
+    h = np.empty(max(1, W.shape[1]))
+    lib().orc_cgs2(W.shape[0], W.shape[1], _ptr(W), W.shape[0], _ptr(w), _ptr(h))
+    return w
+
+
+def norm2(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib().orc_norm2(x.size, _ptr(x)))
+
+
+def gemm(W, Q):
+    W = np.asfortranarray(W, dtype=np.float64)
+    Q = np.asfortranarray(Q, dtype=np.float64)
+    out = np.empty((W.shape[0], Q.shape[1]), order="F")
+    lib().orc_gemm_nn(W.shape[0], W.shape[1], Q.shape[1], _ptr(W), W.shape[0], _ptr(Q),
+                      Q.shape[0], _ptr(out), W.shape[0])
+    return out
+
+
+def splitmix64(x: int) -> int:
+    """SplitMix64 output for state x (golden-ratio increment, then finaliser)."""
+    return int(lib().orc_splitmix64(C.c_uint64(x)))
+
+
+def rng_normal(seed: int, draw: int, n: int):
+    """The counter-based N(0,1) vector (SplitMix64 + Box-Muller) the method draws."""
+    x = np.empty(n)
+    lib().orc_rng_vector(C.c_uint64(seed), C.c_uint64(draw), n, _ptr(x))
+    return x
+
+
+def jacobi_svd(A, max_sweeps: int = 100):
+    """One-sided Jacobi SVD (m >= n); returns (U thin, S desc, V, sweeps or -1)."""
+    A = np.asfortranarray(A, dtype=np.float64)
+    m, n = A.shape
+    if m < n:
+        U, S, V, sw = jacobi_svd(A.T, max_sweeps)
+        return V, S, U, sw
+    S = np.empty(n)
+    U = np.empty((m, n), order="F")
+    V = np.empty((n, n), order="F")
+    sw = lib().orc_jacobi_svd(m, n, _ptr(A), m, _ptr(S), _ptr(U), m, _ptr(V), n, max_sweeps)
+    return U, S, V, sw
+
+
+def sign_normalize(U, V):
+    U = np.array(U, dtype=np.float64, order="F", copy=True)
+    V = np.array(V, dtype=np.float64, order="F", copy=True)
+    lib().orc_sign_normalize(U.shape[0], V.shape[0], U.shape[1], _ptr(U), U.shape[0],
+                             _ptr(V), V.shape[0])
+    return U, V
+
+
+def subspace_dim(k: int, p: int) -> int:
+    return max(15, 3 * k) if p < 0 else k + p
+
+
+def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, seed: int = 0,
+         v0=None, step_budget: int = -1, return_basis: bool = False):
+    """Alg. 2 of the paper: k largest singular triplets of A.
+
+    Returns a dict with S (k), U (m x k), V (n x k), res (k), info (dict) and,
+    if ``return_basis``, the final Lanczos basis Ub (m x t), Vb (n x (t+1))
+    and projected matrix T ((t+1) x (t+1)).  Raises ValueError on bad
+    arguments."""
+    b = _Bound(A)
+    m, n = b.m, b.n
+    t = subspace_dim(k, p)
+    S = np.zeros(k)
+    U = np.zeros((m, k), order="F")
+    V = np.zeros((n, k), order="F")
+    res = np.zeros(k)
+    info = Info()
+    v0a = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64)
+    Ub = Vb = Tb = None
+    if return_basis:
+        Ub = np.zeros((m, t), order="F")
+        Vb = np.zeros((n, t + 1), order="F")
+        Tb = np.zeros((t + 1, t + 1), order="F")
+    rc = lib().orc_svds(C.byref(b.mat), k, p, tol, maxit, C.c_uint64(seed), _ptr(v0a),
+                        step_budget, _ptr(S), _ptr(U), m, _ptr(V), n, _ptr(res),
+                        C.byref(info), _ptr(Ub), _ptr(Vb), _ptr(Tb))
+    if rc == -1:
+        raise ValueError("bad arguments (need 1 <= k <= t, t <= m, t + 1 <= n, tol > 0, maxit >= 1)")
+    if rc != 0:
+        raise MemoryError("oracle ran out of memory")
+    out = {"S": S, "U": U, "V": V, "res": res, "info": info.as_dict(), "t": t}
+    if return_basis:
+        out.update(Ub=Ub, Vb=Vb, T=Tb)
+    return out
