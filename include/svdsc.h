@@ -1,0 +1,189 @@
+/*
+ * svdsc — truncated SVD on one GB300 GPU (sm_103a).
+ *
+ * Computes the k largest singular triplets of a sparse (CSR) or dense matrix A
+ * (m x n):  A ~ U_k diag(S) V_k^T  with S descending and U_k, V_k orthonormal
+ * (the problem of Eq. (1) of the svds-C paper, arXiv 2405.18966, Sec. 2).  The
+ * method is the one Sec. 2.1 describes: Lanczos bidiagonalization (Alg. 1) with
+ * full re-orthogonalization of every new vector (here: two classical
+ * Gram-Schmidt passes, "CGS2"), the Ritz residual test of Eq. (4), and the
+ * augmented restart of Eq. (5)-(7) / Alg. 2.  Every step runs in this
+ * library's CUDA kernels on the device; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *   - Dense matrices are column-major with a leading dimension (the paper's
+ *     `mat` struct, Sec. 2.3).  Vectors are contiguous.
+ *   - "device pointer" means memory the current CUDA device can address
+ *     (cudaMalloc / torch CUDA tensors); "host pointer" means ordinary or
+ *     pinned host memory.  Flags named *on_device select which.
+ *   - Return value: 0 (SVDSC_OK) on success, SVDSC_NOT_CONVERGED (+1) when the
+ *     outputs are written but not every residual reached tol, a negative
+ *     SVDSC_ERR_* code otherwise (outputs then untouched).  svdsc_strerror
+ *     gives a message.  No entry point aborts the process.
+ *   - All work is issued on the stream given to svdsc_create (NULL = the
+ *     legacy default stream); solve synchronizes that stream before it
+ *     returns.  A context must not be used by two host threads at once.
+ */
+#ifndef SVDSC_H
+#define SVDSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SVDSC_OK 0
+#define SVDSC_NOT_CONVERGED 1
+#define SVDSC_ERR_ARG (-1)        /* bad argument (NULL pointer, k < 1, tol <= 0, ...) */
+#define SVDSC_ERR_SIZE (-2)       /* t = k+p does not fit: need t <= m and t+1 <= n */
+#define SVDSC_ERR_CSR (-3)        /* row pointers not monotone or a column index out of range */
+#define SVDSC_ERR_NOMEM (-4)      /* device or host allocation failed */
+#define SVDSC_ERR_CUDA (-5)       /* a CUDA runtime call failed */
+#define SVDSC_ERR_TIMEOUT (-6)    /* a bounded device-side wait ran out */
+#define SVDSC_ERR_NONFINITE (-7)  /* NaN or Inf met in A or in a Lanczos vector */
+
+enum svdsc_format { SVDSC_CSR = 0, SVDSC_DENSE = 1 };
+enum svdsc_precision { SVDSC_FP64 = 0, SVDSC_MIXED = 1 };
+enum svdsc_value_type { SVDSC_F64 = 0, SVDSC_F32 = 1 };
+
+/*
+ * Input matrix (read-only, owned by the caller; svdsc_create copies it, so
+ * the caller may free it as soon as create returns).
+ * CSR (format = SVDSC_CSR), following the paper's `mat_csr` (Sec. 2.3):
+ *   index_base 0 or 1 (the paper's column indices start at 1);
+ *   either row_ptr (m+1 entries, 3-array CSR) or row_begin/row_end (m entries
+ *   each, the MKL 4-array form pointerB/pointerE the paper uses);
+ *   col_idx (nnz entries, int32), values (nnz entries, double or float as
+ *   value_type says).  nnz = row_ptr[m] - row_ptr[0] for 3-array input and is
+ *   taken from the nnz field for 4-array input (the extent of col_idx/values).
+ *   Duplicate (row, col) entries are summed by the products.
+ * Dense (format = SVDSC_DENSE): `dense` column-major m x n, leading dimension
+ *   ld >= m, double only.
+ * on_device = 1: every pointer above is a device pointer; 0: host pointers.
+ */
+typedef struct svdsc_matrix {
+    int32_t format;
+    int32_t index_base;
+    int64_t m, n, nnz;
+    const int64_t *row_ptr;
+    const int64_t *row_begin;
+    const int64_t *row_end;
+    const int32_t *col_idx;
+    const void *values;
+    int32_t value_type;
+    int32_t on_device;
+    const double *dense;
+    int64_t ld;
+} svdsc_matrix;
+
+/*
+ * Options.  precision: SVDSC_FP64 runs every product, projection, norm and the
+ * projected SVD in FP64.  SVDSC_MIXED keeps FP32 copies of A and of the
+ * Lanczos basis for the sparse products and the first CGS pass (the second
+ * pass, all norms, the projected SVD and the residual test stay FP64).
+ * seed selects the counter-based normal generator used for v_1 when no start
+ * vector is given and for replacement vectors after a breakdown.
+ */
+typedef struct svdsc_options {
+    int32_t precision;
+    int32_t reserved;
+    uint64_t seed;
+} svdsc_options;
+
+/* Per-solve report (all fields written by svdsc_solve). */
+typedef struct svdsc_info {
+    int32_t converged;     /* 1 if every res_j < tol */
+    int32_t nconv;         /* number of j < k with res_j < tol */
+    int32_t restarts;      /* augmented restarts performed */
+    int32_t breakdowns;    /* Lanczos vectors replaced by random ones */
+    int64_t n_matvec;      /* products with A or A^T (2t + 2R(t-k)) */
+    int64_t n_steps;       /* Lanczos vectors formed */
+    int64_t n_launches;    /* CUDA kernels this solve launched */
+    double anorm_est;      /* largest alpha, beta or sigma seen (estimate of ||A||_2) */
+    double beta_t;         /* T(t, t+1) of the last projected matrix */
+    int32_t t;             /* subspace dimension used */
+    int32_t reserved;
+} svdsc_info;
+
+typedef struct svdsc_ctx svdsc_ctx;
+
+/*
+ * Copies A to the device and prepares it: converts CSR to 0-based 3-array
+ * form, validates it (SVDSC_ERR_CSR), builds CSR(A^T) and the row-length bins
+ * of both.  `stream` is a cudaStream_t (or NULL).  On success *out owns all
+ * device memory of the solver until svdsc_destroy.
+ */
+int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *opt,
+                 void *stream);
+
+/*
+ * Alg. 2: k largest singular triplets.
+ *   t = k + p (p < 0: t = max(15, 3k), Alg. 2 line 1); needs 1 <= k <= t,
+ *   t <= m and t + 1 <= n (SVDSC_ERR_SIZE otherwise).
+ *   tol: relative residual tolerance of Eq. (4), > 0 (the paper uses 1e-10).
+ *   maxit >= 1: number of projected-SVD-and-test rounds; the last round never
+ *   restarts (at most maxit - 1 restarts).
+ *   v0: start vector (n entries, host or device per v0_on_device) or NULL for
+ *   the seeded random draw.
+ *   Outputs (written on success or SVDSC_NOT_CONVERGED): S[k] descending,
+ *   U (m x k, column-major, ldu >= m), V (n x k, ldv >= n), res[k] (may be
+ *   NULL) with res_j = |beta_t Uh(t,j)| / sigma_j.  Each pair (u_j, v_j) is
+ *   signed so that the entry of v_j with the largest magnitude (lowest index
+ *   on ties) is positive.  out_on_device selects device or host outputs.
+ *   info may be NULL.
+ */
+int svdsc_solve(svdsc_ctx *ctx, int k, int p, double tol, int maxit,
+                const double *v0, int v0_on_device,
+                double *S, double *U, int64_t ldu, double *V, int64_t ldv, double *res,
+                int out_on_device, svdsc_info *info);
+
+/* Frees every device and host resource of ctx (NULL is a no-op). */
+int svdsc_destroy(svdsc_ctx *ctx);
+
+/* Static message for a status code. */
+const char *svdsc_strerror(int status);
+
+/* ---------------------------------------------------------------------------
+ * Component entry points (one hot-path step each, on device pointers, on the
+ * context's stream).  They exist so each kernel can be checked and timed on
+ * its own; svdsc_solve does not need them.
+ */
+
+/*
+ * y = A x (trans = 0, Alg. 1 line 7, x: n, y: m) or y = A^T x (trans = 1,
+ * Alg. 1 line 5, x: m, y: n), minus coef * z when z != NULL (the fused
+ * "- beta_i u_i" / "- alpha_i v_i" term).  FP64 vectors; in MIXED contexts the
+ * sparse product itself runs in FP32 as in the solver.  Device pointers.
+ */
+int svdsc_matvec(svdsc_ctx *ctx, int trans, const double *x, const double *z, double coef,
+                 double *y);
+
+/*
+ * Full re-orthogonalization of Sec. 2.1 as CGS2: w <- (I - W W^T)(I - W W^T) w
+ * for W = the first `ncols` columns of a column-major len x ncols basis with
+ * leading dimension ldw, followed by the norm: *norm_out (device) = ||w||_2.
+ * len must be m or n of the context (its chunking is prepared for those),
+ * ncols <= t_max (the largest t the context has been solved or prepared for,
+ * see svdsc_reserve).  W, w, norm_out: device pointers; w must not alias W.
+ */
+int svdsc_cgs2(svdsc_ctx *ctx, int64_t len, int64_t ncols, const double *W, int64_t ldw,
+               double *w, double *norm_out);
+
+/*
+ * Projected SVD of Alg. 2 line 4 on the device: T is t x t (ldt >= t), any
+ * square matrix (the solver passes the upper-triangular T(1:t,1:t)).  Outputs
+ * S[t] descending, Uh (t x t, ld t) and Vh (t x t, ld t) with T = Uh diag(S)
+ * Vh^T.  FP64 one-sided Jacobi.  Device pointers; t <= t_max.
+ */
+int svdsc_small_svd(svdsc_ctx *ctx, int t, const double *T, int64_t ldt, double *S, double *Uh,
+                    double *Vh);
+
+/* Sizes the context's workspace for subspace dimension t (solve does this
+ * itself; the component entry points need it first). */
+int svdsc_reserve(svdsc_ctx *ctx, int t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVDSC_H */

@@ -1,0 +1,258 @@
+"""svdsc: truncated SVD on one GB300 GPU — Python binding of libsvdsc.so.
+
+This module only marshals arguments to the C-ABI declared in include/svdsc.h
+(ctypes); every step of the solver runs in the library's CUDA kernels.  The
+library must have been built (``python -c "import __graft_entry__ as g;
+g.build()"`` or ``paper_2405_18966_gb300.build.build()``); importing the
+binding without it raises, there is no fallback.
+
+Matrices are given as objects with ``m, n, row_ptr, col_idx, values`` (CSR,
+0- or 1-based, numpy arrays on the host or torch CUDA tensors on the device)
+or as a 2-D numpy array / torch CUDA tensor (dense, column-major copies are
+made as needed).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsvdsc.so")
+
+OK = 0
+NOT_CONVERGED = 1
+ERR_ARG, ERR_SIZE, ERR_CSR, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE = -1, -2, -3, -4, -5, -6, -7
+CSR_FORMAT, DENSE_FORMAT = 0, 1
+FP64, MIXED = 0, 1
+F64, F32 = 0, 1
+
+# Every symbol include/svdsc.h declares.
+EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "svdsc_matvec",
+           "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve")
+
+
+class SvdscMatrix(C.Structure):
+    _fields_ = [("format", C.c_int32), ("index_base", C.c_int32), ("m", C.c_int64),
+                ("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("row_begin", C.c_void_p), ("row_end", C.c_void_p), ("col_idx", C.c_void_p),
+                ("values", C.c_void_p), ("value_type", C.c_int32), ("on_device", C.c_int32),
+                ("dense", C.c_void_p), ("ld", C.c_int64)]
+
+
+class SvdscOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
+
+
+class SvdscInfo(C.Structure):
+    _fields_ = [("converged", C.c_int32), ("nconv", C.c_int32), ("restarts", C.c_int32),
+                ("breakdowns", C.c_int32), ("n_matvec", C.c_int64), ("n_steps", C.c_int64),
+                ("n_launches", C.c_int64), ("anorm_est", C.c_double), ("beta_t", C.c_double),
+                ("t", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_lib = None
+
+
+def lib():
+    """Loads libsvdsc.so; raises if it was not built (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsvdsc.so not built ({LIB_PATH}); run paper_2405_18966_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, dbl, i32 = C.c_void_p, C.c_int64, C.c_double, C.c_int
+        L.svdsc_create.argtypes = [C.POINTER(vp), C.POINTER(SvdscMatrix), C.POINTER(SvdscOptions), vp]
+        L.svdsc_solve.argtypes = [vp, i32, i32, dbl, i32, vp, i32, vp, vp, i64, vp, i64, vp, i32,
+                                  C.POINTER(SvdscInfo)]
+        L.svdsc_destroy.argtypes = [vp]
+        L.svdsc_strerror.argtypes = [i32]
+        L.svdsc_strerror.restype = C.c_char_p
+        L.svdsc_matvec.argtypes = [vp, i32, vp, vp, dbl, vp]
+        L.svdsc_cgs2.argtypes = [vp, i64, i64, vp, i64, vp, vp]
+        L.svdsc_small_svd.argtypes = [vp, i32, vp, i64, vp, vp, vp]
+        L.svdsc_reserve.argtypes = [vp, i32]
+        for name in EXPORTS:
+            getattr(L, name).restype = getattr(L, name).restype or C.c_int
+        L.svdsc_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+class SvdscError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().svdsc_strerror(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+def _check(status: int, where: str) -> int:
+    if status < 0:
+        raise SvdscError(status, where)
+    return status
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return C.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(C.c_void_p)
+
+
+@dataclass
+class Result:
+    S: object
+    U: object
+    V: object
+    res: object
+    info: dict
+    status: int
+
+
+class Solver:
+    """A matrix prepared on the device (svdsc_create) that can be solved many times."""
+
+    def __init__(self, A, precision: str = "fp64", seed: int = 0, stream=None):
+        self._keep = []
+        self.handle = C.c_void_p()
+        prec = {"fp64": FP64, "mixed": MIXED}[precision]
+        mat = SvdscMatrix()
+        if hasattr(A, "row_ptr"):
+            on_dev = _is_torch(A.row_ptr) and A.row_ptr.is_cuda
+            rp, ci, va = A.row_ptr, A.col_idx, A.values
+            if not on_dev:
+                rp = np.ascontiguousarray(rp, dtype=np.int64)
+                ci = np.ascontiguousarray(ci, dtype=np.int32)
+                va = np.ascontiguousarray(va)
+                if va.dtype not in (np.float64, np.float32):
+                    va = va.astype(np.float64)
+            vt = F32 if str(va.dtype).endswith("float32") else F64
+            self._keep += [rp, ci, va]
+            mat.format, mat.index_base = CSR_FORMAT, int(getattr(A, "index_base", 0))
+            mat.m, mat.n = int(A.m), int(A.n)
+            mat.nnz = int(getattr(A, "nnz", 0))
+            mat.row_ptr, mat.col_idx, mat.values = _ptr(rp), _ptr(ci), _ptr(va)
+            mat.value_type, mat.on_device = vt, int(on_dev)
+            self.m, self.n = int(A.m), int(A.n)
+        else:
+            a = A.a if hasattr(A, "a") else A
+            on_dev = _is_torch(a) and a.is_cuda
+            if on_dev:
+                at = a.t().contiguous()  # column-major storage of a
+                self._keep.append(at)
+                mat.dense, mat.ld = _ptr(at), a.shape[0]
+            else:
+                at = np.asfortranarray(a, dtype=np.float64)
+                self._keep.append(at)
+                mat.dense, mat.ld = _ptr(at), at.shape[0]
+            mat.format, mat.on_device = DENSE_FORMAT, int(on_dev)
+            mat.m, mat.n = a.shape[0], a.shape[1]
+            mat.value_type = F64
+            self.m, self.n = int(a.shape[0]), int(a.shape[1])
+        opt = SvdscOptions(prec, 0, seed)
+        st = None if stream is None else C.c_void_p(int(stream))
+        self.stream = stream
+        _check(lib().svdsc_create(C.byref(self.handle), C.byref(mat), C.byref(opt), st), "svdsc_create")
+        self._keep = []  # create copied everything
+
+    def close(self):
+        if self.handle:
+            lib().svdsc_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, v0=None,
+              out: str = "host", outputs=None) -> Result:
+        """Alg. 2: k largest singular triplets.  out='host' returns numpy arrays,
+        out='device' torch CUDA tensors (or writes into `outputs` = (S, U, V, res)
+        preallocated with the matching placement, U/V column-major)."""
+        info = SvdscInfo()
+        if outputs is not None:
+            S, U, V, res = outputs
+            on_dev = _is_torch(S)
+        elif out == "host":
+            S, res = np.zeros(k), np.zeros(k)
+            U = np.zeros((self.m, k), order="F")
+            V = np.zeros((self.n, k), order="F")
+            on_dev = False
+        else:
+            import torch
+            dev = torch.device("cuda", torch.cuda.current_device())
+            S = torch.zeros(k, dtype=torch.float64, device=dev)
+            res = torch.zeros(k, dtype=torch.float64, device=dev)
+            U = torch.zeros((k, self.m), dtype=torch.float64, device=dev)  # column-major m x k
+            V = torch.zeros((k, self.n), dtype=torch.float64, device=dev)
+            on_dev = True
+        v0p, v0dev = None, 0
+        if v0 is not None:
+            if _is_torch(v0):
+                v0p, v0dev = _ptr(v0), int(v0.is_cuda)
+            else:
+                v0 = np.ascontiguousarray(v0, dtype=np.float64)
+                v0p = _ptr(v0)
+        status = _check(lib().svdsc_solve(self.handle, k, p, tol, maxit, v0p, v0dev, _ptr(S), _ptr(U),
+                                          self.m, _ptr(V), self.n, _ptr(res), int(on_dev),
+                                          C.byref(info)), "svdsc_solve")
+        if on_dev and outputs is None:
+            U, V = U.t(), V.t()  # views: m x k and n x k
+        return Result(S, U, V, res, info.as_dict(), status)
+
+    # -- component entry points (device tensors)
+    def matvec(self, x, trans: bool = False, z=None, coef: float = 0.0):
+        import torch
+        y = torch.empty(self.n if trans else self.m, dtype=torch.float64, device=x.device)
+        _check(lib().svdsc_matvec(self.handle, int(trans), _ptr(x), _ptr(z), coef, _ptr(y)), "svdsc_matvec")
+        return y
+
+    def reserve(self, t: int):
+        _check(lib().svdsc_reserve(self.handle, t), "svdsc_reserve")
+
+    def cgs2(self, Wt, w):
+        """Wt: (ncols, ldw) torch tensor = column-major basis; w: length-len vector (modified copy)."""
+        import torch
+        w = w.clone()
+        nrm = torch.empty(1, dtype=torch.float64, device=w.device)
+        ncols, ldw = Wt.shape
+        _check(lib().svdsc_cgs2(self.handle, w.numel(), ncols, _ptr(Wt), ldw, _ptr(w), _ptr(nrm)),
+               "svdsc_cgs2")
+        return w, float(nrm.item())
+
+    def small_svd(self, T):
+        """T: t x t torch CUDA float64 tensor; returns (S, Uh, Vh) with T = Uh diag(S) Vh^T."""
+        import torch
+        t = T.shape[0]
+        Tc = T.t().contiguous()  # column-major
+        S = torch.empty(t, dtype=torch.float64, device=T.device)
+        Uh = torch.empty((t, t), dtype=torch.float64, device=T.device)
+        Vh = torch.empty((t, t), dtype=torch.float64, device=T.device)
+        _check(lib().svdsc_small_svd(self.handle, t, _ptr(Tc), t, _ptr(S), _ptr(Uh), _ptr(Vh)),
+               "svdsc_small_svd")
+        return S, Uh.t(), Vh.t()
+
+
+def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, precision: str = "fp64",
+         seed: int = 0, v0=None, out: str = "host") -> Result:
+    """One-shot convenience: create, solve, destroy."""
+    with Solver(A, precision=precision, seed=seed) as s:
+        return s.solve(k, p, tol, maxit, v0=v0, out=out)

@@ -1,0 +1,108 @@
+// Internal declarations shared by the svdsc CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "../../include/svdsc.h"
+
+namespace svdsc {
+
+// Device-side status block of one context (device memory, read by the host at
+// restart boundaries only).
+struct DevStatus {
+    int poison;        // a finalize met a breakdown or a non-finite norm: later kernels skip
+    int bd_step;       // step id of the first such vector (INT32_MAX: none)
+    int nonfinite;     // the bad norm was NaN/Inf
+    int timeout;       // a bounded grid barrier ran out
+    int converged;     // residual test: every res_j < tol
+    int nconv;         // residual test: count of res_j < tol
+    int svd_sweeps;    // sweeps of the last projected SVD (-1: sweep cap hit)
+    int pad;
+    double anorm[2];   // running max of alpha/beta/sigma, double-buffered by step parity
+    double beta_t;     // T(t, t+1) at the last residual test
+    double last_norm;  // norm of the last finalized vector
+};
+
+// Row chunking of one vector length for the row-blocked kernels.
+struct Chunk {
+    int64_t len = 0;
+    int64_t R = 0;   // rows per CTA (multiple of 64)
+    int nb = 0;      // number of CTAs
+};
+Chunk make_chunk(int64_t len, int target_blocks);
+
+// Row-length bins of a CSR matrix for the binned SpMV kernel.
+constexpr int kNumBins = 7;  // lanes per row: 1,2,4,8,16,32 and a whole CTA
+struct Bins {
+    int64_t row_start[kNumBins + 1] = {0};    // offsets into perm
+    int64_t block_start[kNumBins + 1] = {0};  // CTA offsets of each bin in the single launch
+};
+
+struct DevCSR {
+    int64_t m = 0, n = 0, nnz = 0;
+    int64_t *row_ptr = nullptr;  // m+1, 0-based
+    int32_t *col = nullptr;      // nnz
+    double *val = nullptr;       // nnz (FP64 contexts)
+    float *val32 = nullptr;      // nnz (MIXED contexts)
+    int32_t *perm = nullptr;     // m: rows grouped by bin, ascending inside a bin
+    Bins bins;
+};
+
+struct DevDense {
+    int64_t m = 0, n = 0, ld = 0;
+    double *a = nullptr;
+};
+
+constexpr int kSpmvThreads = 256;
+constexpr int kRowThreads = 256;
+
+// ---- products (spmv.cu)
+// y = A x - coef * z (z may be null; coef from *coef_dev when non-null, else coef_h)
+cudaError_t csr_spmv_f64(const DevCSR &A, const double *x, const double *z, const double *coef_dev,
+                         double coef_h, double *y, const int *poison, cudaStream_t s);
+cudaError_t csr_spmv_f32(const DevCSR &A, const float *x, const double *z, const double *coef_dev,
+                         double coef_h, double *y, const int *poison, cudaStream_t s);
+cudaError_t dense_gemv_n(const DevDense &A, const double *x, const double *z, const double *coef_dev,
+                         double coef_h, double *y, double *partial, const int *poison,
+                         cudaStream_t s, int *launches);
+cudaError_t dense_gemv_t(const DevDense &A, const double *x, const double *z, const double *coef_dev,
+                         double coef_h, double *y, double *partial, const int *poison,
+                         cudaStream_t s, int *launches);
+size_t dense_partial_doubles(const DevDense &A);
+// create-time preparation
+int csr_prepare(const svdsc_matrix *in, bool want_f32, bool want_f64, DevCSR *A, DevCSR *AT,
+                cudaStream_t s);
+void csr_free(DevCSR *A);
+
+// ---- re-orthogonalization (reorth.cu)
+void proj_partial(const double *W, int64_t ld, int ncols, const double *w, const Chunk &c,
+                  double *P, const int *poison, cudaStream_t s);
+void proj_partial_f32(const float *W32, int64_t ld, int ncols, const double *w, const Chunk &c,
+                      double *P, const int *poison, cudaStream_t s);
+void proj_reduce(const double *P, int nb, int ncols, double *h, const int *poison, cudaStream_t s);
+void update_sub(const double *W, int64_t ld, int ncols, const double *h, double *w, const Chunk &c,
+                double *Pn, const int *poison, cudaStream_t s);
+void update_sub_f32(const float *W32, int64_t ld, int ncols, const double *h, double *w,
+                    const Chunk &c, const int *poison, cudaStream_t s);
+void norm_partial(const double *w, const Chunk &c, double *Pn, const int *poison, cudaStream_t s);
+// mode: 0 = Lanczos vector (T entry := norm, breakdown check), 1 = plain normalise
+// (no T entry), 2 = repair of a breakdown (T entry := 0, needs norm > 1e-8)
+void finalize(double *w, const Chunk &c, const double *Pn, double *T_entry, DevStatus *st,
+              int step, int parity, int mode, float *w32, cudaStream_t s);
+void rng_normal_vec(uint64_t seed, uint64_t draw, int64_t len, double *x, cudaStream_t s);
+void copy_f64_to_f32(const double *x, float *y, int64_t len, cudaStream_t s);
+
+// ---- projected SVD (small_svd.cu)
+struct SvdWork {
+    double *B = nullptr;       // t x t
+    double *W = nullptr;       // t x t (right rotations)
+    double *sig = nullptr;     // t
+    int *rot = nullptr;        // per-sweep rotation counters
+    unsigned *bar = nullptr;   // grid barrier: [count, generation]
+    int max_sweeps = 60;
+    int coop_blocks = 0;       // co-resident CTAs available for the multi-CTA kernel
+};
+cudaError_t small_svd(int t, const double *T, int64_t ldt, double *S, double *Uh, double *Vh,
+                      SvdWork &w, DevStatus *st, cudaStream_t s, int *launches);
+int small_svd_coop_capacity();
+
+}  // namespace svdsc

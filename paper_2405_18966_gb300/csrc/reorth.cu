@@ -1,0 +1,343 @@
+// Full re-orthogonalization (Sec. 2.1 of the svds-C paper) as CGS2 on the
+// device: h = W^T w (GEMV-T, per-CTA partial sums over row chunks + an ordered
+// reduction), w -= W h (GEMV-N, fused with the partial sums of ||w||^2 on the
+// last pass), then the norm / breakdown test / scaling of Alg. 1 lines 3, 6, 8.
+// Every reduction runs in a fixed order, so results are bitwise reproducible.
+#include <cstdint>
+#include <cstdio>
+#include "internal.cuh"
+
+namespace svdsc {
+
+Chunk make_chunk(int64_t len, int target_blocks)
+{
+    Chunk c;
+    c.len = len;
+    int64_t R = (len + target_blocks - 1) / target_blocks;
+    R = (R + 63) & ~int64_t(63);
+    if (R < 256) R = 256;
+    if (R > 4096) R = 4096;
+    c.R = R;
+    c.nb = (int)((len + R - 1) / R);
+    if (c.nb < 1) c.nb = 1;
+    return c;
+}
+
+__device__ __forceinline__ bool poisoned(const int *poison)
+{
+    return poison && *(volatile const int *)poison;
+}
+
+// ---------------------------------------------------------------- GEMV-T
+
+constexpr int kProjWarps = 16;
+
+// P[c * nb + b] = sum over the rows of chunk b of W(r, c) * w(r)
+template <typename WT>
+__global__ void __launch_bounds__(kProjWarps * 32)
+proj_partial_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__restrict__ w,
+                    int64_t len, int64_t R, int nb, double *__restrict__ P, const int *poison)
+{
+    if (poisoned(poison)) return;
+    extern __shared__ double ws[];
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    const int rows = (int)min(R, len - r0);
+    for (int j = threadIdx.x; j < rows; j += blockDim.x) ws[j] = w[r0 + j];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = warp; c < ncols; c += kProjWarps) {
+        const WT *col = W + (int64_t)c * ld + r0;
+        double s;
+        if constexpr (sizeof(WT) == 8) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int j = 2 * lane;
+            for (; j + 65 < rows; j += 128) {
+                const double2 v0 = __ldcs((const double2 *)(col + j));
+                const double2 v1 = __ldcs((const double2 *)(col + j + 64));
+                a0 = fma(v0.x, ws[j], a0);
+                a1 = fma(v0.y, ws[j + 1], a1);
+                a2 = fma(v1.x, ws[j + 64], a2);
+                a3 = fma(v1.y, ws[j + 65], a3);
+            }
+            for (; j < rows; j += 64) {
+                a0 = fma((double)col[j], ws[j], a0);
+                if (j + 1 < rows) a1 = fma((double)col[j + 1], ws[j + 1], a1);
+            }
+            s = (a0 + a1) + (a2 + a3);
+        } else {
+            // FP32 shadow (first CGS pass of the mixed form): FP32 products and sums
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            int j = 4 * lane;
+            for (; j + 3 < rows; j += 128) {
+                const float4 v = __ldcs((const float4 *)(col + j));
+                a0 = fmaf(v.x, (float)ws[j], a0);
+                a1 = fmaf(v.y, (float)ws[j + 1], a1);
+                a2 = fmaf(v.z, (float)ws[j + 2], a2);
+                a3 = fmaf(v.w, (float)ws[j + 3], a3);
+            }
+            // this lane's last, partial group of four
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (j + q < rows) a0 = fmaf((float)col[j + q], (float)ws[j + q], a0);
+            s = (double)((a0 + a1) + (a2 + a3));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) P[(int64_t)c * nb + blockIdx.x] = s;
+    }
+}
+
+void proj_partial(const double *W, int64_t ld, int ncols, const double *w, const Chunk &c,
+                  double *P, const int *poison, cudaStream_t s)
+{
+    if (ncols <= 0) return;
+    proj_partial_kernel<double><<<c.nb, kProjWarps * 32, sizeof(double) * c.R, s>>>(
+        W, ld, ncols, w, c.len, c.R, c.nb, P, poison);
+}
+
+void proj_partial_f32(const float *W32, int64_t ld, int ncols, const double *w, const Chunk &c,
+                      double *P, const int *poison, cudaStream_t s)
+{
+    if (ncols <= 0) return;
+    proj_partial_kernel<float><<<c.nb, kProjWarps * 32, sizeof(double) * c.R, s>>>(
+        W32, ld, ncols, w, c.len, c.R, c.nb, P, poison);
+}
+
+// h[c] = sum over b of P[c * nb + b], in a fixed order.
+__global__ void __launch_bounds__(128)
+proj_reduce_kernel(const double *__restrict__ P, int nb, double *__restrict__ h, const int *poison)
+{
+    if (poisoned(poison)) return;
+    const double *p = P + (int64_t)blockIdx.x * nb;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 128) s += p[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[4];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) h[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+void proj_reduce(const double *P, int nb, int ncols, double *h, const int *poison, cudaStream_t s)
+{
+    if (ncols <= 0) return;
+    proj_reduce_kernel<<<ncols, 128, 0, s>>>(P, nb, h, poison);
+}
+
+// ---------------------------------------------------------------- GEMV-N
+
+__device__ __forceinline__ double block_sum_256(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
+    }
+    return t;
+}
+
+// w(r) -= sum_c W(r, c) h(c) over chunk rows; Pn[b] = sum of the new w(r)^2
+template <typename WT>
+__global__ void __launch_bounds__(kRowThreads)
+update_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__restrict__ h,
+              double *__restrict__ w, int64_t len, int64_t R, double *__restrict__ Pn,
+              const int *poison)
+{
+    if (poisoned(poison)) return;
+    extern __shared__ double hs[];
+    __shared__ double red[kRowThreads / 32];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = h[c];
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    const int rows = (int)min(R, len - r0);
+    double nrm = 0.0;
+    for (int j = 2 * threadIdx.x; j < rows; j += 2 * kRowThreads) {
+        const int64_t r = r0 + j;
+        if (j + 1 < rows) {
+            double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+            const WT *p = W + r;
+            int c = 0;
+            if constexpr (sizeof(WT) == 8) {
+                for (; c + 1 < ncols; c += 2) {
+                    const double2 v0 = __ldcs((const double2 *)(p + (int64_t)c * ld));
+                    const double2 v1 = __ldcs((const double2 *)(p + (int64_t)(c + 1) * ld));
+                    a0 = fma(v0.x, hs[c], a0);
+                    a1 = fma(v0.y, hs[c], a1);
+                    b0 = fma(v1.x, hs[c + 1], b0);
+                    b1 = fma(v1.y, hs[c + 1], b1);
+                }
+                for (; c < ncols; c++) {
+                    const double2 v0 = __ldcs((const double2 *)(p + (int64_t)c * ld));
+                    a0 = fma(v0.x, hs[c], a0);
+                    a1 = fma(v0.y, hs[c], a1);
+                }
+            } else {
+                float f0 = 0.f, f1 = 0.f, g0 = 0.f, g1 = 0.f;
+                for (; c + 1 < ncols; c += 2) {
+                    const float2 v0 = __ldcs((const float2 *)(p + (int64_t)c * ld));
+                    const float2 v1 = __ldcs((const float2 *)(p + (int64_t)(c + 1) * ld));
+                    f0 = fmaf(v0.x, (float)hs[c], f0);
+                    f1 = fmaf(v0.y, (float)hs[c], f1);
+                    g0 = fmaf(v1.x, (float)hs[c + 1], g0);
+                    g1 = fmaf(v1.y, (float)hs[c + 1], g1);
+                }
+                for (; c < ncols; c++) {
+                    const float2 v0 = __ldcs((const float2 *)(p + (int64_t)c * ld));
+                    f0 = fmaf(v0.x, (float)hs[c], f0);
+                    f1 = fmaf(v0.y, (float)hs[c], f1);
+                }
+                a0 = (double)f0; a1 = (double)f1; b0 = (double)g0; b1 = (double)g1;
+            }
+            const double n0 = w[r] - (a0 + b0);
+            const double n1 = w[r + 1] - (a1 + b1);
+            w[r] = n0;
+            w[r + 1] = n1;
+            nrm = fma(n0, n0, nrm);
+            nrm = fma(n1, n1, nrm);
+        } else {
+            double a0 = 0.0;
+            for (int c = 0; c < ncols; c++) a0 = fma((double)W[r + (int64_t)c * ld], hs[c], a0);
+            const double n0 = w[r] - a0;
+            w[r] = n0;
+            nrm = fma(n0, n0, nrm);
+        }
+    }
+    if (Pn) {
+        const double t = block_sum_256(nrm, red);
+        if (threadIdx.x == 0) Pn[blockIdx.x] = t;
+    }
+}
+
+void update_sub(const double *W, int64_t ld, int ncols, const double *h, double *w, const Chunk &c,
+                double *Pn, const int *poison, cudaStream_t s)
+{
+    if (ncols <= 0 && !Pn) return;
+    update_kernel<double><<<c.nb, kRowThreads, sizeof(double) * (ncols > 0 ? ncols : 1), s>>>(
+        W, ld, ncols, h, w, c.len, c.R, Pn, poison);
+}
+
+void update_sub_f32(const float *W32, int64_t ld, int ncols, const double *h, double *w,
+                    const Chunk &c, const int *poison, cudaStream_t s)
+{
+    if (ncols <= 0) return;
+    update_kernel<float><<<c.nb, kRowThreads, sizeof(double) * ncols, s>>>(W32, ld, ncols, h, w, c.len,
+                                                                          c.R, nullptr, poison);
+}
+
+__global__ void __launch_bounds__(kRowThreads)
+norm_partial_kernel(const double *__restrict__ w, int64_t len, int64_t R, double *__restrict__ Pn,
+                    const int *poison)
+{
+    if (poisoned(poison)) return;
+    __shared__ double red[kRowThreads / 32];
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    const int rows = (int)min(R, len - r0);
+    double nrm = 0.0;
+    for (int j = threadIdx.x; j < rows; j += kRowThreads) nrm = fma(w[r0 + j], w[r0 + j], nrm);
+    const double t = block_sum_256(nrm, red);
+    if (threadIdx.x == 0) Pn[blockIdx.x] = t;
+}
+
+void norm_partial(const double *w, const Chunk &c, double *Pn, const int *poison, cudaStream_t s)
+{
+    norm_partial_kernel<<<c.nb, kRowThreads, 0, s>>>(w, c.len, c.R, Pn, poison);
+}
+
+// ---------------------------------------------------------------- finalize
+
+__global__ void __launch_bounds__(kRowThreads)
+finalize_kernel(double *__restrict__ w, int64_t len, int64_t R, const double *__restrict__ Pn, int nb,
+                double *T_entry, DevStatus *st, int step, int parity, int mode, float *w32)
+{
+    if (*(volatile int *)&st->poison) return;
+    __shared__ double red[kRowThreads / 32];
+    __shared__ double s_nrm;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kRowThreads) v += Pn[b];
+    const double tot = block_sum_256(v, red);
+    if (threadIdx.x == 0) s_nrm = sqrt(tot);
+    __syncthreads();
+    const double nrm = s_nrm;
+    const double anorm = st->anorm[parity];
+    bool bad;
+    if (mode == 0) bad = !(nrm > 1e-13 * anorm) || !isfinite(nrm);
+    else if (mode == 2) bad = !(nrm > 1e-8) || !isfinite(nrm);
+    else bad = !(nrm > 0.0) || !isfinite(nrm);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (bad) {
+            atomicMin(&st->bd_step, step);
+            if (!isfinite(nrm)) st->nonfinite = 1;
+            st->poison = 1;
+        }
+        if (mode == 0 && T_entry) *T_entry = bad ? 0.0 : nrm;
+        if (mode == 2 && T_entry) *T_entry = 0.0;
+        st->anorm[parity ^ 1] = (mode == 0 && !bad && nrm > anorm) ? nrm : anorm;
+        st->last_norm = nrm;
+    }
+    if (bad) return;
+    const double inv = 1.0 / nrm;
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    const int rows = (int)min(R, len - r0);
+    for (int j = threadIdx.x; j < rows; j += kRowThreads) {
+        const double x = w[r0 + j] * inv;
+        w[r0 + j] = x;
+        if (w32) w32[r0 + j] = (float)x;
+    }
+}
+
+void finalize(double *w, const Chunk &c, const double *Pn, double *T_entry, DevStatus *st, int step,
+              int parity, int mode, float *w32, cudaStream_t s)
+{
+    finalize_kernel<<<c.nb, kRowThreads, 0, s>>>(w, c.len, c.R, Pn, c.nb, T_entry, st, step, parity,
+                                                 mode, w32);
+}
+
+// ---------------------------------------------------------------- random draws
+// Counter-based N(0,1): SplitMix64 (Steele, Lea & Flood 2014) as the mixing
+// function and the Box-Muller transform (1958).  Element j of draw d under
+// seed: key = mix(seed); c = 2 (d 2^32 + j); U1, U2 from mix(key + c) and
+// mix(key + c + 1) (top 53 bits, offset by one half); z = sqrt(-2 ln U1) cos(2 pi U2).
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void rng_normal_kernel(uint64_t seed, uint64_t draw, int64_t len, double *x)
+{
+    const uint64_t key = splitmix_mix(seed);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = 2ull * ((draw << 32) + (uint64_t)j);
+        const double u1 = ((double)(splitmix_mix(key + c) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double u2 = ((double)(splitmix_mix(key + c + 1ull) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        x[j] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    }
+}
+
+void rng_normal_vec(uint64_t seed, uint64_t draw, int64_t len, double *x, cudaStream_t s)
+{
+    const int64_t blocks = std::min<int64_t>((len + 255) / 256, 4 * 152);
+    rng_normal_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(seed, draw, len, x);
+}
+
+__global__ void f64_to_f32_kernel(const double *__restrict__ x, float *__restrict__ y, int64_t len)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len;
+         j += (int64_t)gridDim.x * blockDim.x)
+        y[j] = (float)x[j];
+}
+
+void copy_f64_to_f32(const double *x, float *y, int64_t len, cudaStream_t s)
+{
+    const int64_t blocks = std::min<int64_t>((len + 255) / 256, 8 * 152);
+    f64_to_f32_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(x, y, len);
+}
+
+}  // namespace svdsc

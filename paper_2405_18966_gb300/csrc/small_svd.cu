@@ -1,0 +1,388 @@
+// Projected SVD of Alg. 2 line 4 (svds-C paper): [Uh, Sh, Vh] = svd(T(1:t,1:t))
+// in FP64 on the device, by one-sided (Hestenes) Jacobi: columns of B = T V
+// are rotated in pairs until mutually orthogonal; sigma_j = ||B(:,j)||,
+// uh_j = B(:,j)/sigma_j, vh_j = the accumulated rotation.  Pairs are visited
+// in round-robin (circle) order so that t/2 disjoint rotations run at once:
+//   t <= 64 : one CTA, B and V in shared memory, one warp per pair;
+//   t  > 64 : a cooperative multi-CTA kernel (one pair per CTA per round,
+//             B and V in global memory, bounded grid barrier between rounds),
+// since GB300 has ~2 FP64 FMA/clk/SM and an O(t^3) sweep must be spread over
+// many SMs.  The convergence test matches the CPU oracle's:
+// |b_p . b_q| <= eps sqrt(t) ||b_p|| ||b_q||.
+#include <cfloat>
+#include <cstdint>
+#include "internal.cuh"
+
+namespace svdsc {
+
+__device__ __forceinline__ void rr_pair(int slot, int round, int n2, int *p, int *q)
+{
+    auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (n2 - 1)) + 1; };
+    int a = player(slot), b = player(n2 - 1 - slot);
+    *p = a < b ? a : b;
+    *q = a < b ? b : a;
+}
+
+// rotation of Golub & Van Loan (one-sided Jacobi): zeroes gamma in
+// [alpha gamma; gamma beta]; same formula as the oracle.
+__device__ __forceinline__ bool jacobi_rotation(double alpha, double beta, double gamma, double tol,
+                                                double *c, double *s)
+{
+    if (gamma == 0.0 || fabs(gamma) <= tol * sqrt(alpha * beta)) return false;
+    const double zeta = (beta - alpha) / (2.0 * gamma);
+    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    *c = 1.0 / sqrt(1.0 + tt * tt);
+    *s = *c * tt;
+    return true;
+}
+
+// Completes columns with sigma == 0 to an orthonormal set: the first unit
+// vectors that survive two Gram-Schmidt passes against the other columns
+// (same rule as the oracle).  One CTA; Uh column-major t x t (ld t).
+__device__ void complete_zero_columns(int t, double *Uh, const double *S)
+{
+    __shared__ double red[32];
+    __shared__ double s_val;
+    int next_e = 0;
+    for (int j = 0; j < t; j++) {
+        if (S[j] > 0.0) continue;
+        double *u = Uh + (int64_t)j * t;
+        while (next_e < t) {
+            for (int r = threadIdx.x; r < t; r += blockDim.x) u[r] = (r == next_e) ? 1.0 : 0.0;
+            next_e++;
+            __syncthreads();
+            for (int pass = 0; pass < 2; pass++) {
+                for (int i = 0; i < t; i++) {
+                    if (i == j || (S[i] == 0.0 && i > j)) continue;
+                    const double *ui = Uh + (int64_t)i * t;
+                    double d = 0.0;
+                    for (int r = threadIdx.x; r < t; r += blockDim.x) d += ui[r] * u[r];
+                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        double tot = 0.0;
+                        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += red[w];
+                        s_val = tot;
+                    }
+                    __syncthreads();
+                    d = s_val;
+                    for (int r = threadIdx.x; r < t; r += blockDim.x) u[r] -= d * ui[r];
+                    __syncthreads();
+                }
+            }
+            double q = 0.0;
+            for (int r = threadIdx.x; r < t; r += blockDim.x) q += u[r] * u[r];
+            for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += red[w];
+                s_val = sqrt(tot);
+            }
+            __syncthreads();
+            const double nu = s_val;
+            if (nu > 0.5) {
+                for (int r = threadIdx.x; r < t; r += blockDim.x) u[r] /= nu;
+                __syncthreads();
+                break;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------ one-CTA form
+constexpr int kSmallT = 64;
+constexpr int kSmallThreads = 1024;
+
+__global__ void __launch_bounds__(kSmallThreads)
+jacobi_small_kernel(int t, const double *__restrict__ T, int64_t ldt, double *__restrict__ S,
+                    double *__restrict__ Uh, double *__restrict__ Vh, DevStatus *st, int max_sweeps)
+{
+    extern __shared__ double sm[];
+    double *B = sm;                       // t x t, ld kSmallT
+    double *W = sm + kSmallT * kSmallT;   // t x t, ld kSmallT
+    __shared__ double sig[kSmallT];
+    __shared__ int rot_count;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < t * t; i += blockDim.x) {
+        const int r = i % t, c = i / t;
+        B[r + c * kSmallT] = T[r + (int64_t)c * ldt];
+        W[r + c * kSmallT] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const double tol = DBL_EPSILON * sqrt((double)t);
+    const int n2 = t + (t & 1);
+    int sweeps = 0;
+    bool conv = false;
+    while (sweeps < max_sweeps) {
+        if (threadIdx.x == 0) rot_count = 0;
+        __syncthreads();
+        sweeps++;
+        for (int round = 0; round < n2 - 1; round++) {
+            for (int slot = warp; slot < n2 / 2; slot += nwarps) {
+                int p, q;
+                rr_pair(slot, round, n2, &p, &q);
+                if (q >= t) continue;
+                double *bp = B + p * kSmallT, *bq = B + q * kSmallT;
+                double a = 0.0, b = 0.0, g = 0.0;
+                for (int r = lane; r < t; r += 32) {
+                    a += bp[r] * bp[r];
+                    b += bq[r] * bq[r];
+                    g += bp[r] * bq[r];
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    g += __shfl_xor_sync(0xffffffffu, g, o);
+                }
+                double c, s;
+                if (!jacobi_rotation(a, b, g, tol, &c, &s)) continue;
+                if (lane == 0) atomicAdd(&rot_count, 1);
+                for (int r = lane; r < t; r += 32) {
+                    const double x = bp[r], y = bq[r];
+                    bp[r] = c * x - s * y;
+                    bq[r] = s * x + c * y;
+                }
+                double *wp = W + p * kSmallT, *wq = W + q * kSmallT;
+                for (int r = lane; r < t; r += 32) {
+                    const double x = wp[r], y = wq[r];
+                    wp[r] = c * x - s * y;
+                    wq[r] = s * x + c * y;
+                }
+            }
+            __syncthreads();
+        }
+        if (rot_count == 0) { conv = true; break; }
+        __syncthreads();
+    }
+    // singular values, descending stable order, outputs
+    for (int j = warp; j < t; j += nwarps) {
+        double a = 0.0;
+        for (int r = lane; r < t; r += 32) a += B[r + j * kSmallT] * B[r + j * kSmallT];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) sig[j] = sqrt(a);
+    }
+    __syncthreads();
+    for (int j = warp; j < t; j += nwarps) {
+        const double sj = sig[j];
+        int rank = 0;
+        for (int i = 0; i < t; i++) rank += (sig[i] > sj) || (sig[i] == sj && i < j);
+        if (lane == 0) S[rank] = sj;
+        for (int r = lane; r < t; r += 32) {
+            Uh[r + (int64_t)rank * t] = sj > 0.0 ? B[r + j * kSmallT] / sj : 0.0;
+            Vh[r + (int64_t)rank * t] = W[r + j * kSmallT];
+        }
+    }
+    __syncthreads();
+    if (sig[0] >= 0.0) {  // zero singular values are rare: check on the sorted list
+        bool anyzero = false;
+        for (int j = 0; j < t; j++) anyzero |= (sig[j] == 0.0);
+        if (anyzero) complete_zero_columns(t, Uh, S);
+    }
+    if (threadIdx.x == 0) st->svd_sweeps = conv ? sweeps : -1;
+}
+
+// ------------------------------------------------------------ multi-CTA form
+constexpr int kCoopThreads = 256;
+
+// Bounded grid barrier for a cooperative launch (all CTAs co-resident).
+// bar[0]: arrivals, bar[1]: generation.  Gives up after ~0.5-1 s of spinning,
+// records the timeout and returns false.
+__device__ bool grid_sync(unsigned *bar, unsigned nblk, int *timeout)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (arrived == nblk - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > (1ull << 23)) { ok = 0; atomicExch(timeout, 1); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && !*(volatile int *)timeout;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ double block_sum_coop(double v, double *red, double *out)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int w = 0; w < kCoopThreads / 32; w++) tsum += red[w];
+        *out = tsum;
+    }
+    __syncthreads();
+    return *out;
+}
+
+__global__ void __launch_bounds__(kCoopThreads)
+jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, double *W,
+                   double *sig, int *rot, unsigned *bar, DevStatus *st, int max_sweeps,
+                   double *__restrict__ S, double *__restrict__ Uh, double *__restrict__ Vh)
+{
+    __shared__ double red[3][kCoopThreads / 32];
+    __shared__ double sv[3];
+    const unsigned nblk = gridDim.x;
+    int *timeout = &st->timeout;
+    // B = T, W = I
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)t * t;
+         i += (int64_t)nblk * blockDim.x) {
+        const int r = (int)(i % t), c = (int)(i / t);
+        __stcg(B + i, T[r + (int64_t)c * ldt]);
+        __stcg(W + i, (r == c) ? 1.0 : 0.0);
+    }
+    if (!grid_sync(bar, nblk, timeout)) return;
+    const double tol = DBL_EPSILON * sqrt((double)t);
+    const int n2 = t + (t & 1);
+    int sweeps = 0;
+    bool conv = false;
+    while (sweeps < max_sweeps) {
+        for (int round = 0; round < n2 - 1; round++) {
+            for (int slot = blockIdx.x; slot < n2 / 2; slot += nblk) {
+                int p, q;
+                rr_pair(slot, round, n2, &p, &q);
+                if (q >= t) continue;
+                double *bp = B + (int64_t)p * t, *bq = B + (int64_t)q * t;
+                double a = 0.0, b = 0.0, g = 0.0;
+                for (int r = threadIdx.x; r < t; r += kCoopThreads) {
+                    const double x = __ldcg(bp + r), y = __ldcg(bq + r);
+                    a += x * x;
+                    b += y * y;
+                    g += x * y;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    g += __shfl_xor_sync(0xffffffffu, g, o);
+                }
+                if ((threadIdx.x & 31) == 0) {
+                    red[0][threadIdx.x >> 5] = a;
+                    red[1][threadIdx.x >> 5] = b;
+                    red[2][threadIdx.x >> 5] = g;
+                }
+                __syncthreads();
+                if (threadIdx.x < 3) {
+                    double tsum = 0.0;
+                    for (int w = 0; w < kCoopThreads / 32; w++) tsum += red[threadIdx.x][w];
+                    sv[threadIdx.x] = tsum;
+                }
+                __syncthreads();
+                double c, s;
+                const bool do_rot = jacobi_rotation(sv[0], sv[1], sv[2], tol, &c, &s);
+                __syncthreads();
+                if (!do_rot) continue;
+                if (threadIdx.x == 0) atomicAdd(rot + sweeps, 1);
+                for (int r = threadIdx.x; r < t; r += kCoopThreads) {
+                    const double x = __ldcg(bp + r), y = __ldcg(bq + r);
+                    __stcg(bp + r, c * x - s * y);
+                    __stcg(bq + r, s * x + c * y);
+                }
+                double *wp = W + (int64_t)p * t, *wq = W + (int64_t)q * t;
+                for (int r = threadIdx.x; r < t; r += kCoopThreads) {
+                    const double x = __ldcg(wp + r), y = __ldcg(wq + r);
+                    __stcg(wp + r, c * x - s * y);
+                    __stcg(wq + r, s * x + c * y);
+                }
+            }
+            if (!grid_sync(bar, nblk, timeout)) return;
+        }
+        const int done = (__ldcg(rot + sweeps) == 0);
+        sweeps++;
+        if (done) { conv = true; break; }
+    }
+    for (int j = blockIdx.x; j < t; j += nblk) {
+        const double *bj = B + (int64_t)j * t;
+        double a = 0.0;
+        for (int r = threadIdx.x; r < t; r += kCoopThreads) {
+            const double x = __ldcg(bj + r);
+            a += x * x;
+        }
+        const double tot = block_sum_coop(a, red[0], &sv[0]);
+        if (threadIdx.x == 0) __stcg(sig + j, sqrt(tot));
+    }
+    if (!grid_sync(bar, nblk, timeout)) return;
+    for (int j = blockIdx.x; j < t; j += nblk) {
+        const double sj = __ldcg(sig + j);
+        int rank = 0;
+        for (int i = 0; i < t; i++) {
+            const double si = __ldcg(sig + i);
+            rank += (si > sj) || (si == sj && i < j);
+        }
+        if (threadIdx.x == 0) S[rank] = sj;
+        for (int r = threadIdx.x; r < t; r += kCoopThreads) {
+            Uh[r + (int64_t)rank * t] = sj > 0.0 ? __ldcg(B + r + (int64_t)j * t) / sj : 0.0;
+            Vh[r + (int64_t)rank * t] = __ldcg(W + r + (int64_t)j * t);
+        }
+    }
+    if (!grid_sync(bar, nblk, timeout)) return;
+    if (blockIdx.x == 0) {
+        bool anyzero = false;
+        for (int j = 0; j < t; j++) anyzero |= (__ldcg(sig + j) == 0.0);
+        if (anyzero) complete_zero_columns(t, Uh, S);
+        if (threadIdx.x == 0) st->svd_sweeps = conv ? sweeps : -1;
+    }
+}
+
+int small_svd_coop_capacity()
+{
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_coop_kernel, kCoopThreads, 0) !=
+        cudaSuccess)
+        return 0;
+    return nsm * per;
+}
+
+cudaError_t small_svd(int t, const double *T, int64_t ldt, double *S, double *Uh, double *Vh,
+                      SvdWork &w, DevStatus *st, cudaStream_t s, int *launches)
+{
+    if (t <= kSmallT) {
+        const size_t smem = 2 * sizeof(double) * kSmallT * kSmallT;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(jacobi_small_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        jacobi_small_kernel<<<1, kSmallThreads, smem, s>>>(t, T, ldt, S, Uh, Vh, st, 100);
+        if (launches) (*launches)++;
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(w.rot, 0, sizeof(int) * w.max_sweeps, s);
+    if (e != cudaSuccess) return e;
+    int nblk = (t + (t & 1)) / 2;
+    if (nblk > w.coop_blocks) nblk = w.coop_blocks;
+    if (nblk < 1) return cudaErrorInvalidConfiguration;
+    int tt = t;
+    int64_t ld = ldt;
+    int ms = w.max_sweeps;
+    void *args[] = {&tt, (void *)&T, &ld, &w.B, &w.W, &w.sig, &w.rot, &w.bar, &st, &ms, &S, &Uh, &Vh};
+    e = cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel, dim3(nblk), dim3(kCoopThreads),
+                                    args, 0, s);
+    if (launches) (*launches)++;
+    return e;
+}
+
+}  // namespace svdsc

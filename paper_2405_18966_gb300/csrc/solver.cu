@@ -1,0 +1,776 @@
+// Host driver and C-ABI of the svdsc library: Alg. 2 of the svds-C paper
+// (augmented-restart truncated SVD) with every numerical step on the device.
+// The host issues kernels and reads a small status block once per restart
+// round (convergence flag, breakdown marker); nothing else crosses to the host
+// until the outputs are copied.
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+#include "internal.cuh"
+
+using namespace svdsc;
+
+struct StepRec {
+    int side;    // 0: u (column of U), 1: v (column of V)
+    int col;     // column index created
+    int parity;  // anorm parity used by its finalize
+};
+
+struct svdsc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int precision = SVDSC_FP64;
+    uint64_t seed = 0;
+    int format = SVDSC_CSR;
+    int64_t m = 0, n = 0;
+    DevCSR A, AT;
+    DevDense D;
+    double *dense_part = nullptr;
+    Chunk cm, cn;
+    // workspace sized for t_cap
+    int t_cap = 0;
+    int64_t ldu = 0, ldv = 0;
+    double *U = nullptr, *V = nullptr, *T = nullptr;
+    float *U32 = nullptr, *V32 = nullptr;
+    double *P = nullptr, *h = nullptr, *Pn = nullptr;
+    double *Sh = nullptr, *Uh = nullptr, *Vh = nullptr, *res = nullptr, *rho = nullptr;
+    SvdWork svd;
+    DevStatus *st = nullptr;
+    DevStatus *st_host = nullptr;  // pinned
+    // per-solve state
+    int64_t launches = 0;
+    int parity = 0;
+    int t = 0, k = 0;
+    uint64_t draws = 0;
+    int breakdowns = 0;
+    int64_t n_matvec = 0, n_steps = 0;
+    std::vector<StepRec> steps;
+};
+
+#define CU(x)                                          \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return SVDSC_ERR_CUDA;  \
+    } while (0)
+
+static inline double *colU(svdsc_ctx *c, int j) { return c->U + (int64_t)j * c->ldu; }
+static inline double *colV(svdsc_ctx *c, int j) { return c->V + (int64_t)j * c->ldv; }
+static inline float *colU32(svdsc_ctx *c, int j) { return c->U32 ? c->U32 + (int64_t)j * c->ldu : nullptr; }
+static inline float *colV32(svdsc_ctx *c, int j) { return c->V32 ? c->V32 + (int64_t)j * c->ldv : nullptr; }
+static inline double *Tent(svdsc_ctx *c, int r, int col) { return c->T + r + (int64_t)col * (c->t + 1); }
+static inline int *poison_ptr(svdsc_ctx *c) { return &c->st->poison; }
+
+// ----------------------------------------------------------- small kernels
+
+// Eq. (4) residuals res_j = |beta_t Uh(t,j)| / max(sigma_j, eps sigma_1), the
+// restart coefficients rho_j = beta_t Uh(t,j) of Eq. (6), the convergence test
+// of Alg. 2 line 5 and the ||A|| estimate.
+__global__ void residual_kernel(int t, int k, double tol, const double *__restrict__ T,
+                                const double *__restrict__ Sh, const double *__restrict__ Uh,
+                                double *__restrict__ res, double *__restrict__ rho, DevStatus *st,
+                                int parity)
+{
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const double beta_t = T[(t - 1) + (int64_t)t * (t + 1)];
+    const double s0 = Sh[0];
+    int local = 0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const double den = Sh[j] > DBL_EPSILON * s0 ? Sh[j] : DBL_EPSILON * s0;
+        const double u = Uh[(t - 1) + (int64_t)j * t];
+        const double r = den > 0.0 ? fabs(beta_t * u) / den : 0.0;
+        res[j] = r;
+        rho[j] = beta_t * u;
+        local += (r < tol);
+    }
+    atomicAdd(&cnt, local);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->nconv = cnt;
+        st->converged = (cnt == k);
+        st->beta_t = beta_t;
+        if (s0 > st->anorm[parity]) st->anorm[parity] = s0;
+    }
+}
+
+// T <- 0; T(j,j) = sigma_j, T(j,k+1) = rho_j for j <= k  (Alg. 2 line 9)
+__global__ void restart_T_kernel(int t, int k, double *__restrict__ T, const double *__restrict__ Sh,
+                                 const double *__restrict__ rho)
+{
+    const int64_t ld = t + 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ld * ld;
+         i += (int64_t)gridDim.x * blockDim.x)
+        T[i] = 0.0;
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < k; j += blockDim.x) {
+            T[j + j * ld] = Sh[j];
+            T[j + (int64_t)k * ld] = rho[j];
+        }
+}
+
+// In-place restart update W(:, 0:k) <- W(:, 0:t) Q(:, 0:k) of Alg. 2 line 8 /
+// line 15 (FP64 FMA).  A CTA owns a block of 32 rows and all k outputs of
+// them, so it reads its rows completely before overwriting them.  Q is held in
+// shared memory in chunks of KC rows.
+constexpr int kGemmGroups = 8;   // warps per CTA; each covers 32 rows x (k / 8) columns
+constexpr int kGemmMaxQ = 32;    // accumulators per thread => k <= 256
+
+__global__ void __launch_bounds__(kGemmGroups * 32)
+gemm_inplace_kernel(double *__restrict__ W, int64_t ld, int64_t rows, int t,
+                    const double *__restrict__ Q, int64_t ldq, int k, int KC)
+{
+    extern __shared__ double Qs[];  // KC x k, ld KC
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int nq = (k + kGemmGroups - 1) / kGemmGroups;
+    for (int64_t rb = (int64_t)blockIdx.x * 32; rb < rows; rb += (int64_t)gridDim.x * 32) {
+        double acc[kGemmMaxQ];
+#pragma unroll
+        for (int q = 0; q < kGemmMaxQ; q++) acc[q] = 0.0;
+        const int64_t r = rb + lane;
+        for (int c0 = 0; c0 < t; c0 += KC) {
+            const int kc = min(KC, t - c0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < kc * k; i += blockDim.x) {
+                const int cc = i % kc, j = i / kc;
+                Qs[cc + j * KC] = Q[(c0 + cc) + (int64_t)j * ldq];
+            }
+            __syncthreads();
+            for (int cc = 0; cc < kc; cc++) {
+                const double a = (r < rows) ? W[r + (int64_t)(c0 + cc) * ld] : 0.0;
+#pragma unroll
+                for (int q = 0; q < kGemmMaxQ; q++) {
+                    if (q < nq) {
+                        const int j = grp + kGemmGroups * q;
+                        if (j < k) acc[q] = fma(a, Qs[cc + j * KC], acc[q]);
+                    }
+                }
+            }
+        }
+        __syncthreads();  // every read of this row block precedes the writes
+        if (r < rows) {
+#pragma unroll
+            for (int q = 0; q < kGemmMaxQ; q++) {
+                const int j = grp + kGemmGroups * q;
+                if (q < nq && j < k) W[r + (int64_t)j * ld] = acc[q];
+            }
+        }
+    }
+}
+
+static int gemm_inplace(svdsc_ctx *c, double *W, int64_t ld, int64_t rows, int t, const double *Q,
+                        int k)
+{
+    if (k > kGemmGroups * kGemmMaxQ) return SVDSC_ERR_SIZE;
+    int KC = t;
+    const int max_doubles = (200 * 1024) / 8;
+    if ((int64_t)KC * k > max_doubles) KC = std::max(1, max_doubles / k);
+    const size_t smem = sizeof(double) * (size_t)KC * k;
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        CU(cudaFuncSetAttribute(gemm_inplace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024));
+        attr = 200 * 1024;
+    }
+    const int64_t blocks = std::min<int64_t>((rows + 31) / 32, 152 * (smem > 100 * 1024 ? 1 : 2));
+    gemm_inplace_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), kGemmGroups * 32, smem, c->stream>>>(
+        W, ld, rows, t, Q, t, k, KC);
+    c->launches++;
+    CU(cudaGetLastError());
+    return SVDSC_OK;
+}
+
+// Sign rule for returned pairs: the entry of v_j with the largest magnitude
+// (lowest index on ties) is made positive, flipping u_j with it.
+__global__ void __launch_bounds__(256)
+sign_kernel(double *__restrict__ U, int64_t ldu, int64_t m, double *__restrict__ V, int64_t ldv,
+            int64_t n)
+{
+    const int j = blockIdx.x;
+    double *v = V + (int64_t)j * ldv;
+    double best = -1.0;
+    int64_t bi = 0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+        const double a = fabs(v[r]);
+        if (a > best) { best = a; bi = r; }  // ascending r: first max kept
+    }
+    __shared__ double sb[256];
+    __shared__ int64_t si[256];
+    sb[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double b2 = sb[threadIdx.x + o];
+            const int64_t i2 = si[threadIdx.x + o];
+            if (b2 > sb[threadIdx.x] || (b2 == sb[threadIdx.x] && i2 < si[threadIdx.x])) {
+                sb[threadIdx.x] = b2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    const bool flip = v[si[0]] < 0.0;
+    __syncthreads();
+    if (!flip) return;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) v[r] = -v[r];
+    double *u = U + (int64_t)j * ldu;
+    for (int64_t r = threadIdx.x; r < m; r += blockDim.x) u[r] = -u[r];
+}
+
+__global__ void sum_sqrt_kernel(const double *__restrict__ Pn, int nb, double *out)
+{
+    __shared__ double red[8];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += Pn[b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        *out = sqrt(t);
+    }
+}
+
+__global__ void check_finite_kernel(const double *__restrict__ a, int64_t ld, int64_t m, int64_t n,
+                                    int *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m * n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i % m, c = i / m;
+        if (!isfinite(a[r + c * ld])) { atomicOr(bad, 1); return; }
+    }
+}
+
+// ----------------------------------------------------------- host helpers
+
+static void free_workspace(svdsc_ctx *c)
+{
+    cudaFree(c->U); cudaFree(c->V); cudaFree(c->T);
+    cudaFree(c->U32); cudaFree(c->V32);
+    cudaFree(c->P); cudaFree(c->h); cudaFree(c->Pn);
+    cudaFree(c->Sh); cudaFree(c->Uh); cudaFree(c->Vh); cudaFree(c->res); cudaFree(c->rho);
+    cudaFree(c->svd.B); cudaFree(c->svd.W); cudaFree(c->svd.sig); cudaFree(c->svd.rot);
+    cudaFree(c->svd.bar);
+    c->U = c->V = c->T = c->P = c->h = c->Pn = c->Sh = c->Uh = c->Vh = c->res = c->rho = nullptr;
+    c->U32 = c->V32 = nullptr;
+    c->svd.B = c->svd.W = c->svd.sig = nullptr;
+    c->svd.rot = nullptr;
+    c->svd.bar = nullptr;
+    c->t_cap = 0;
+}
+
+static int reserve_ws(svdsc_ctx *c, int t)
+{
+    if (t <= c->t_cap) return SVDSC_OK;
+    cudaStreamSynchronize(c->stream);
+    free_workspace(c);
+    const int64_t cols = t + 2;
+    const int nbmax = std::max(c->cm.nb, c->cn.nb);
+    bool ok = true;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) ok = false;
+    };
+    alloc((void **)&c->U, sizeof(double) * c->ldu * cols);
+    alloc((void **)&c->V, sizeof(double) * c->ldv * cols);
+    alloc((void **)&c->T, sizeof(double) * (size_t)(t + 2) * (t + 2));
+    if (c->precision == SVDSC_MIXED) {
+        alloc((void **)&c->U32, sizeof(float) * c->ldu * cols);
+        alloc((void **)&c->V32, sizeof(float) * c->ldv * cols);
+    }
+    alloc((void **)&c->P, sizeof(double) * (size_t)nbmax * cols);
+    alloc((void **)&c->h, sizeof(double) * cols);
+    alloc((void **)&c->Pn, sizeof(double) * nbmax);
+    alloc((void **)&c->Sh, sizeof(double) * t);
+    alloc((void **)&c->Uh, sizeof(double) * (size_t)t * t);
+    alloc((void **)&c->Vh, sizeof(double) * (size_t)t * t);
+    alloc((void **)&c->res, sizeof(double) * t);
+    alloc((void **)&c->rho, sizeof(double) * t);
+    alloc((void **)&c->svd.B, sizeof(double) * (size_t)t * t);
+    alloc((void **)&c->svd.W, sizeof(double) * (size_t)t * t);
+    alloc((void **)&c->svd.sig, sizeof(double) * t);
+    alloc((void **)&c->svd.rot, sizeof(int) * c->svd.max_sweeps);
+    alloc((void **)&c->svd.bar, sizeof(unsigned) * 2);
+    if (!ok) {
+        free_workspace(c);
+        cudaGetLastError();
+        return SVDSC_ERR_NOMEM;
+    }
+    // zero the bases once so that stale columns never hold NaN
+    if (cudaMemsetAsync(c->U, 0, sizeof(double) * c->ldu * cols, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->V, 0, sizeof(double) * c->ldv * cols, c->stream) != cudaSuccess)
+        return SVDSC_ERR_CUDA;
+    c->t_cap = t;
+    return SVDSC_OK;
+}
+
+// y = A x - coef z   (trans: A^T).  x32 is the FP32 copy of x in MIXED contexts.
+static int apply_A(svdsc_ctx *c, int trans, const double *x, const float *x32, const double *z,
+                   const double *coef_dev, double coef_h, double *y, const int *poison)
+{
+    cudaError_t e;
+    if (c->format == SVDSC_CSR) {
+        const DevCSR &M = trans ? c->AT : c->A;
+        if (c->precision == SVDSC_MIXED) e = csr_spmv_f32(M, x32, z, coef_dev, coef_h, y, poison, c->stream);
+        else e = csr_spmv_f64(M, x, z, coef_dev, coef_h, y, poison, c->stream);
+        c->launches++;
+    } else {
+        int l = 0;
+        if (trans) e = dense_gemv_t(c->D, x, z, coef_dev, coef_h, y, c->dense_part, poison, c->stream, &l);
+        else e = dense_gemv_n(c->D, x, z, coef_dev, coef_h, y, c->dense_part, poison, c->stream, &l);
+        c->launches += l;
+    }
+    c->n_matvec++;
+    return e == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
+}
+
+// CGS2: w <- (I - W W^T)^2 w against ncols columns; leaves the partial sums
+// of ||w||^2 in c->Pn.  MIXED: first pass on the FP32 shadow W32.
+static void cgs2(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, int ncols, double *w,
+                 const Chunk &ch, const int *poison)
+{
+    cudaStream_t s = c->stream;
+    if (ncols > 0) {
+        if (W32) {
+            proj_partial_f32(W32, ld, ncols, w, ch, c->P, poison, s);
+            proj_reduce(c->P, ch.nb, ncols, c->h, poison, s);
+            update_sub_f32(W32, ld, ncols, c->h, w, ch, poison, s);
+        } else {
+            proj_partial(W, ld, ncols, w, ch, c->P, poison, s);
+            proj_reduce(c->P, ch.nb, ncols, c->h, poison, s);
+            update_sub(W, ld, ncols, c->h, w, ch, nullptr, poison, s);
+        }
+        proj_partial(W, ld, ncols, w, ch, c->P, poison, s);
+        proj_reduce(c->P, ch.nb, ncols, c->h, poison, s);
+        update_sub(W, ld, ncols, c->h, w, ch, c->Pn, poison, s);
+        c->launches += 6;
+    } else {
+        norm_partial(w, ch, c->Pn, poison, s);
+        c->launches += 1;
+    }
+}
+
+static void do_finalize(svdsc_ctx *c, int side, int col, double *T_entry, int mode)
+{
+    const Chunk &ch = side == 0 ? c->cm : c->cn;
+    double *w = side == 0 ? colU(c, col) : colV(c, col);
+    float *w32 = side == 0 ? colU32(c, col) : colV32(c, col);
+    const int step = (int)c->steps.size();
+    c->steps.push_back({side, col, c->parity});
+    finalize(w, ch, c->Pn, T_entry, c->st, step, c->parity, mode, w32, c->stream);
+    c->parity ^= 1;
+    c->launches++;
+    c->n_steps++;
+}
+
+// v_{i+1} = A^T u_i - alpha_i v_i, CGS2 against v_1..v_i, beta_i = ||.||  (Alg. 1 lines 5-6)
+static int issue_v(svdsc_ctx *c, int i)
+{
+    double *out = colV(c, i);
+    int rc = apply_A(c, 1, colU(c, i - 1), colU32(c, i - 1), colV(c, i - 1), Tent(c, i - 1, i - 1), 0.0,
+                     out, poison_ptr(c));
+    if (rc) return rc;
+    cgs2(c, c->V, c->V32, c->ldv, i, out, c->cn, poison_ptr(c));
+    do_finalize(c, 1, i, Tent(c, i - 1, i), 0);
+    return SVDSC_OK;
+}
+
+// u_{i+1} = A v_{i+1} - beta_i u_i, CGS2 against u_1..u_i, alpha_{i+1}  (Alg. 1 lines 7-8)
+static int issue_u(svdsc_ctx *c, int i)
+{
+    double *out = colU(c, i);
+    int rc = apply_A(c, 0, colV(c, i), colV32(c, i), colU(c, i - 1), Tent(c, i - 1, i), 0.0, out,
+                     poison_ptr(c));
+    if (rc) return rc;
+    cgs2(c, c->U, c->U32, c->ldu, i, out, c->cm, poison_ptr(c));
+    do_finalize(c, 0, i, Tent(c, i, i), 0);
+    return SVDSC_OK;
+}
+
+// Alg. 1 loop for iterations i = s..t (u_{t+1} is not formed); if first_u,
+// iteration s starts with its u half (the v half was already formed).
+static int issue_segment(svdsc_ctx *c, int s, bool first_u)
+{
+    for (int i = s; i <= c->t; i++) {
+        if (!(first_u && i == s)) {
+            int rc = issue_v(c, i);
+            if (rc) return rc;
+        }
+        if (i < c->t) {
+            int rc = issue_u(c, i);
+            if (rc) return rc;
+        }
+    }
+    return SVDSC_OK;
+}
+
+static int read_status(svdsc_ctx *c)
+{
+    CU(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return SVDSC_OK;
+}
+
+// Waits for the issued work; while a Lanczos vector broke down, replaces it
+// by a random vector orthogonalized against its predecessors (T entry 0) and
+// re-issues the rest of the segment.
+static int settle(svdsc_ctx *c)
+{
+    int rc = read_status(c);
+    if (rc) return rc;
+    int guard = 0;
+    while (c->st_host->poison) {
+        if (c->st_host->nonfinite) return SVDSC_ERR_NONFINITE;
+        if (c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
+        if (++guard > 4 * (c->t + 2)) return SVDSC_ERR_NONFINITE;
+        const int sb = c->st_host->bd_step;
+        if (sb < 0 || sb >= (int)c->steps.size()) return SVDSC_ERR_CUDA;
+        const StepRec rec = c->steps[sb];
+        c->breakdowns++;
+        bool repaired = false;
+        for (int attempt = 0; attempt < 8 && !repaired; attempt++) {
+            DevStatus fresh = *c->st_host;
+            fresh.poison = 0;
+            fresh.bd_step = INT_MAX;
+            fresh.nonfinite = 0;
+            CU(cudaMemcpyAsync(c->st, &fresh, sizeof(DevStatus), cudaMemcpyHostToDevice, c->stream));
+            c->parity = rec.parity ^ 1;  // anorm slot written by the failed finalize
+            double *w = rec.side == 0 ? colU(c, rec.col) : colV(c, rec.col);
+            const Chunk &ch = rec.side == 0 ? c->cm : c->cn;
+            rng_normal_vec(c->seed, c->draws++, ch.len, w, c->stream);
+            c->launches++;
+            if (rec.side == 0) cgs2(c, c->U, nullptr, c->ldu, rec.col, w, ch, poison_ptr(c));
+            else cgs2(c, c->V, nullptr, c->ldv, rec.col, w, ch, poison_ptr(c));
+            double *Te = nullptr;
+            if (rec.side == 0) Te = Tent(c, rec.col, rec.col);
+            else Te = Tent(c, rec.col - 1, rec.col);
+            do_finalize(c, rec.side, rec.col, Te, 2);
+            rc = read_status(c);
+            if (rc) return rc;
+            repaired = !c->st_host->poison;
+            if (!repaired && c->st_host->nonfinite) return SVDSC_ERR_NONFINITE;
+        }
+        if (!repaired) return SVDSC_ERR_NONFINITE;
+        // resume after the repaired vector
+        if (rec.side == 1) rc = issue_segment(c, rec.col, true);
+        else rc = issue_segment(c, rec.col + 1, false);
+        if (rc) return rc;
+        rc = read_status(c);
+        if (rc) return rc;
+    }
+    if (c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
+    return SVDSC_OK;
+}
+
+// ----------------------------------------------------------------- C-ABI
+
+extern "C" {
+
+const char *svdsc_strerror(int status)
+{
+    switch (status) {
+    case SVDSC_OK: return "ok";
+    case SVDSC_NOT_CONVERGED: return "not every residual reached tol within maxit rounds";
+    case SVDSC_ERR_ARG: return "bad argument";
+    case SVDSC_ERR_SIZE: return "subspace dimension does not fit (need t <= m, t + 1 <= n, k <= 256)";
+    case SVDSC_ERR_CSR: return "invalid CSR (row pointers or column indices)";
+    case SVDSC_ERR_NOMEM: return "out of memory";
+    case SVDSC_ERR_CUDA: return "CUDA runtime error";
+    case SVDSC_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+    case SVDSC_ERR_NONFINITE: return "NaN or Inf in the matrix or a Lanczos vector";
+    default: return "unknown status";
+    }
+}
+
+int svdsc_destroy(svdsc_ctx *c)
+{
+    if (!c) return SVDSC_OK;
+    cudaStreamSynchronize(c->stream);
+    free_workspace(c);
+    csr_free(&c->A);
+    csr_free(&c->AT);
+    cudaFree(c->D.a);
+    cudaFree(c->dense_part);
+    cudaFree(c->st);
+    cudaFreeHost(c->st_host);
+    delete c;
+    return SVDSC_OK;
+}
+
+int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *opt, void *stream)
+{
+    if (!out || !A) return SVDSC_ERR_ARG;
+    *out = nullptr;
+    if (A->m < 1 || A->n < 1) return SVDSC_ERR_ARG;
+    if (A->format != SVDSC_CSR && A->format != SVDSC_DENSE) return SVDSC_ERR_ARG;
+    const int prec = opt ? opt->precision : SVDSC_FP64;
+    if (prec != SVDSC_FP64 && prec != SVDSC_MIXED) return SVDSC_ERR_ARG;
+    if (A->format == SVDSC_CSR) {
+        if (!A->col_idx || !A->values) return SVDSC_ERR_ARG;
+        if (!A->row_ptr && !(A->row_begin && A->row_end)) return SVDSC_ERR_ARG;
+        if (A->index_base != 0 && A->index_base != 1) return SVDSC_ERR_ARG;
+        if (A->value_type != SVDSC_F64 && A->value_type != SVDSC_F32) return SVDSC_ERR_ARG;
+        if (A->m > INT32_MAX || A->n > INT32_MAX) return SVDSC_ERR_SIZE;
+    } else {
+        if (!A->dense || A->ld < A->m) return SVDSC_ERR_ARG;
+        if (prec == SVDSC_MIXED) return SVDSC_ERR_ARG;  // the mixed form is defined for CSR input
+    }
+    svdsc_ctx *c = new (std::nothrow) svdsc_ctx();
+    if (!c) return SVDSC_ERR_NOMEM;
+    c->stream = (cudaStream_t)stream;
+    c->precision = prec;
+    c->seed = opt ? opt->seed : 0;
+    c->format = A->format;
+    c->m = A->m;
+    c->n = A->n;
+    c->ldu = (A->m + 63) & ~int64_t(63);
+    c->ldv = (A->n + 63) & ~int64_t(63);
+    c->cm = make_chunk(A->m, 2 * 152);
+    c->cn = make_chunk(A->n, 2 * 152);
+    int rc = SVDSC_OK;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return SVDSC_ERR_CUDA; }
+    if (cudaMalloc(&c->st, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMallocHost(&c->st_host, sizeof(DevStatus)) != cudaSuccess) {
+        svdsc_destroy(c);
+        return SVDSC_ERR_NOMEM;
+    }
+    c->svd.coop_blocks = small_svd_coop_capacity();
+    if (A->format == SVDSC_CSR) {
+        rc = csr_prepare(A, prec == SVDSC_MIXED, prec == SVDSC_FP64, &c->A, &c->AT, c->stream);
+    } else {
+        c->D.m = A->m;
+        c->D.n = A->n;
+        c->D.ld = c->ldu;
+        if (cudaMalloc(&c->D.a, sizeof(double) * (size_t)c->D.ld * A->n) != cudaSuccess) rc = SVDSC_ERR_NOMEM;
+        if (!rc && cudaMemcpy2DAsync(c->D.a, sizeof(double) * c->D.ld, A->dense, sizeof(double) * A->ld,
+                                     sizeof(double) * A->m, A->n,
+                                     A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                     c->stream) != cudaSuccess)
+            rc = SVDSC_ERR_CUDA;
+        if (!rc && cudaMalloc(&c->dense_part, sizeof(double) * dense_partial_doubles(c->D)) != cudaSuccess)
+            rc = SVDSC_ERR_NOMEM;
+        if (!rc) {
+            int *bad = nullptr;
+            int hbad = 0;
+            if (cudaMalloc(&bad, sizeof(int)) != cudaSuccess) rc = SVDSC_ERR_NOMEM;
+            if (!rc) {
+                cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
+                check_finite_kernel<<<8 * 152, 256, 0, c->stream>>>(c->D.a, c->D.ld, c->D.m, c->D.n, bad);
+                if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                    cudaStreamSynchronize(c->stream) != cudaSuccess)
+                    rc = SVDSC_ERR_CUDA;
+                else if (hbad)
+                    rc = SVDSC_ERR_NONFINITE;
+                cudaFree(bad);
+            }
+        }
+    }
+    if (rc) {
+        svdsc_destroy(c);
+        cudaGetLastError();
+        return rc;
+    }
+    *out = c;
+    return SVDSC_OK;
+}
+
+int svdsc_reserve(svdsc_ctx *c, int t)
+{
+    if (!c || t < 1) return SVDSC_ERR_ARG;
+    return reserve_ws(c, t);
+}
+
+int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double *v0, int v0_on_device,
+                double *S, double *U, int64_t ldu, double *V, int64_t ldv, double *res,
+                int out_on_device, svdsc_info *info)
+{
+    if (!c || k < 1 || !(tol > 0.0) || maxit < 1 || !S || !U || !V) return SVDSC_ERR_ARG;
+    if (ldu < c->m || ldv < c->n) return SVDSC_ERR_ARG;
+    const int t = (p < 0) ? std::max(15, 3 * k) : k + p;
+    if (t < k || t > c->m || t + 1 > c->n || k > kGemmGroups * kGemmMaxQ) return SVDSC_ERR_SIZE;
+    int rc = reserve_ws(c, t);
+    if (rc) return rc;
+    cudaStream_t s = c->stream;
+    c->t = t;
+    c->k = k;
+    c->launches = 0;
+    c->parity = 0;
+    c->draws = 0;
+    c->breakdowns = 0;
+    c->n_matvec = 0;
+    c->n_steps = 0;
+    c->steps.clear();
+    c->steps.reserve(4 * (size_t)t);
+    {
+        DevStatus init;
+        memset(&init, 0, sizeof(init));
+        init.bd_step = INT_MAX;
+        *c->st_host = init;
+        CU(cudaMemcpyAsync(c->st, c->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+    }
+    CU(cudaMemsetAsync(c->T, 0, sizeof(double) * (size_t)(t + 1) * (t + 1), s));
+
+    // Alg. 1 line 1: v_1 (the caller's v0 or draw 0), normalised
+    if (v0) CU(cudaMemcpyAsync(colV(c, 0), v0, sizeof(double) * c->n,
+                               v0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    else { rng_normal_vec(c->seed, 0, c->n, colV(c, 0), s); c->launches++; }
+    c->draws = 1;
+    norm_partial(colV(c, 0), c->cn, c->Pn, nullptr, s);
+    c->launches++;
+    do_finalize(c, 1, 0, nullptr, 1);
+    rc = read_status(c);
+    if (rc) return rc;
+    if (c->st_host->poison) {  // unusable v0: fall back to a random draw
+        DevStatus fresh = *c->st_host;
+        fresh.poison = 0;
+        fresh.bd_step = INT_MAX;
+        fresh.nonfinite = 0;
+        CU(cudaMemcpyAsync(c->st, &fresh, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+        c->parity = 0;
+        rng_normal_vec(c->seed, c->draws++, c->n, colV(c, 0), s);
+        norm_partial(colV(c, 0), c->cn, c->Pn, nullptr, s);
+        c->launches += 2;
+        do_finalize(c, 1, 0, nullptr, 1);
+    }
+    c->steps.clear();   // step ids below index Lanczos vectors only
+    c->n_steps = 0;
+    // lines 2-3: u_1 = A v_1, alpha_1
+    rc = apply_A(c, 0, colV(c, 0), colV32(c, 0), nullptr, nullptr, 0.0, colU(c, 0), poison_ptr(c));
+    if (rc) return rc;
+    norm_partial(colU(c, 0), c->cm, c->Pn, poison_ptr(c), s);
+    c->launches++;
+    do_finalize(c, 0, 0, Tent(c, 0, 0), 0);
+    // Alg. 2 line 2: LBP(A, t+1)
+    rc = issue_segment(c, 1, false);
+    if (rc) return rc;
+    rc = settle(c);
+    if (rc) return rc;
+
+    int restarts = 0;
+    for (int it = 1; it <= maxit; it++) {
+        // line 4: SVD of T(1:t,1:t)
+        CU(small_svd(t, c->T, t + 1, c->Sh, c->Uh, c->Vh, c->svd, c->st, s, nullptr));
+        c->launches++;
+        // line 5: residual test (Eq. 4)
+        residual_kernel<<<1, 256, 0, s>>>(t, k, tol, c->T, c->Sh, c->Uh, c->res, c->rho, c->st, c->parity);
+        c->launches++;
+        CU(cudaGetLastError());
+        rc = read_status(c);
+        if (rc) return rc;
+        if (c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
+        if (c->st_host->converged || it == maxit) break;
+        // lines 8-12: augmented restart
+        rc = gemm_inplace(c, c->U, c->ldu, c->m, t, c->Uh, k);   // U~_k = U(:,1:t) Uh(:,1:k)
+        if (rc) return rc;
+        rc = gemm_inplace(c, c->V, c->ldv, c->n, t, c->Vh, k);   // V~_k = V(:,1:t) Vh(:,1:k)
+        if (rc) return rc;
+        CU(cudaMemcpyAsync(colV(c, k), colV(c, t), sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+        if (c->precision == SVDSC_MIXED) {
+            copy_f64_to_f32(c->U, c->U32, c->ldu * k, s);
+            copy_f64_to_f32(c->V, c->V32, c->ldv * (k + 1), s);
+            c->launches += 2;
+        }
+        restart_T_kernel<<<1, 256, 0, s>>>(t, k, c->T, c->Sh, c->rho);
+        c->launches++;
+        CU(cudaGetLastError());
+        // u_{k+1} = A v_{k+1} - U~_k rho (Eq. 7), re-orthogonalized against U~_k
+        rc = apply_A(c, 0, colV(c, k), colV32(c, k), nullptr, nullptr, 0.0, colU(c, k), poison_ptr(c));
+        if (rc) return rc;
+        update_sub(c->U, c->ldu, k, c->rho, colU(c, k), c->cm, nullptr, poison_ptr(c), s);
+        c->launches++;
+        cgs2(c, c->U, c->U32, c->ldu, k, colU(c, k), c->cm, poison_ptr(c));
+        do_finalize(c, 0, k, Tent(c, k, k), 0);
+        restarts++;
+        // line 12: continue Alg. 1 from i = k+1
+        rc = issue_segment(c, k + 1, false);
+        if (rc) return rc;
+        rc = settle(c);
+        if (rc) return rc;
+    }
+    const DevStatus fin = *c->st_host;
+
+    // lines 14-15: outputs (in place in the basis, then copied out)
+    rc = gemm_inplace(c, c->U, c->ldu, c->m, t, c->Uh, k);
+    if (rc) return rc;
+    rc = gemm_inplace(c, c->V, c->ldv, c->n, t, c->Vh, k);
+    if (rc) return rc;
+    sign_kernel<<<k, 256, 0, s>>>(c->U, c->ldu, c->m, c->V, c->ldv, c->n);
+    c->launches++;
+    CU(cudaGetLastError());
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CU(cudaMemcpyAsync(S, c->Sh, sizeof(double) * k, kind, s));
+    if (res) CU(cudaMemcpyAsync(res, c->res, sizeof(double) * k, kind, s));
+    CU(cudaMemcpy2DAsync(U, sizeof(double) * ldu, c->U, sizeof(double) * c->ldu, sizeof(double) * c->m, k,
+                         kind, s));
+    CU(cudaMemcpy2DAsync(V, sizeof(double) * ldv, c->V, sizeof(double) * c->ldv, sizeof(double) * c->n, k,
+                         kind, s));
+    CU(cudaStreamSynchronize(s));
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->converged = fin.converged;
+        info->nconv = fin.nconv;
+        info->restarts = restarts;
+        info->breakdowns = c->breakdowns;
+        info->n_matvec = c->n_matvec;
+        info->n_steps = c->n_steps;
+        info->n_launches = c->launches;
+        info->anorm_est = std::max(fin.anorm[0], fin.anorm[1]);
+        info->beta_t = fin.beta_t;
+        info->t = t;
+    }
+    return fin.converged ? SVDSC_OK : SVDSC_NOT_CONVERGED;
+}
+
+int svdsc_matvec(svdsc_ctx *c, int trans, const double *x, const double *z, double coef, double *y)
+{
+    if (!c || !x || !y || (trans != 0 && trans != 1)) return SVDSC_ERR_ARG;
+    float *x32 = nullptr;
+    if (c->precision == SVDSC_MIXED) {
+        const int64_t len = trans ? c->m : c->n;
+        if (cudaMalloc(&x32, sizeof(float) * len) != cudaSuccess) return SVDSC_ERR_NOMEM;
+        copy_f64_to_f32(x, x32, len, c->stream);
+    }
+    const int64_t saved = c->n_matvec;
+    int rc = apply_A(c, trans, x, x32, z, nullptr, coef, y, nullptr);
+    c->n_matvec = saved;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = SVDSC_ERR_CUDA;
+    cudaFree(x32);
+    return rc;
+}
+
+int svdsc_cgs2(svdsc_ctx *c, int64_t len, int64_t ncols, const double *W, int64_t ldw, double *w,
+               double *norm_out)
+{
+    if (!c || !W || !w || !norm_out || ncols < 0 || ldw < len) return SVDSC_ERR_ARG;
+    if (((uintptr_t)W & 15) || ((uintptr_t)w & 15) || (ldw & 1)) return SVDSC_ERR_ARG;
+    const Chunk *ch = (len == c->m) ? &c->cm : (len == c->n ? &c->cn : nullptr);
+    if (!ch) return SVDSC_ERR_ARG;
+    if (ncols > c->t_cap + 1) return SVDSC_ERR_SIZE;
+    cgs2(c, W, nullptr, ldw, (int)ncols, w, *ch, nullptr);
+    sum_sqrt_kernel<<<1, 256, 0, c->stream>>>(c->Pn, ch->nb, norm_out);
+    if (cudaGetLastError() != cudaSuccess) return SVDSC_ERR_CUDA;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
+}
+
+int svdsc_small_svd(svdsc_ctx *c, int t, const double *T, int64_t ldt, double *S, double *Uh, double *Vh)
+{
+    if (!c || t < 1 || !T || !S || !Uh || !Vh || ldt < t) return SVDSC_ERR_ARG;
+    if (t > c->t_cap) return SVDSC_ERR_SIZE;
+    DevStatus init;
+    memset(&init, 0, sizeof(init));
+    init.bd_step = INT_MAX;
+    CU(cudaMemcpyAsync(c->st, &init, sizeof(DevStatus), cudaMemcpyHostToDevice, c->stream));
+    CU(small_svd(t, T, ldt, S, Uh, Vh, c->svd, c->st, c->stream, nullptr));
+    int rc = read_status(c);
+    if (rc) return rc;
+    if (c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
+    return SVDSC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, and exports every
+symbol the public header declares.  No compute call (no GPU here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"^\s*(?:int|const char \*)\s*(svdsc_\w+)\s*\(", text, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2405_18966_gb300 import build
+    return build.build()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for want in ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT\s+(svdsc_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_loads_and_lists_exports(libpath):
+    import paper_2405_18966_gb300 as pkg
+    L = pkg.lib()
+    assert set(pkg.EXPORTS) == set(_declared())
+    for n in pkg.EXPORTS:
+        assert hasattr(L, n)
+    assert L.svdsc_strerror(pkg.ERR_CSR).decode().startswith("invalid CSR")
+    assert L.svdsc_strerror(pkg.NOT_CONVERGED)
+
+
+def test_bad_arguments_rejected_without_gpu(libpath):
+    import ctypes as C
+    import paper_2405_18966_gb300 as pkg
+    L = pkg.lib()
+    h = C.c_void_p()
+    assert L.svdsc_create(C.byref(h), None, None, None) == pkg.ERR_ARG
+    m = pkg.SvdscMatrix()
+    m.format, m.m, m.n = 0, 0, 5
+    assert L.svdsc_create(C.byref(h), C.byref(m), None, None) == pkg.ERR_ARG
+    assert L.svdsc_solve(None, 1, 1, 1e-10, 1, None, 0, None, None, 1, None, 1, None, 0, None) == pkg.ERR_ARG
+    assert L.svdsc_destroy(None) == pkg.OK
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_2405_18966_gb300 as pkg
+    monkeypatch.setattr(pkg, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(pkg, "_lib", None)
+    with pytest.raises(RuntimeError):
+        pkg.lib()
+
+
+def test_oracle_builds_independently():
+    """The oracle and the CUDA sources share no file, header or include."""
+    import oracle
+    oracle.build()
+    src = open(os.path.join(ROOT, "oracle", "svds_oracle.c")).read()
+    assert "#include \"" not in src
+    csrc = os.path.join(ROOT, "paper_2405_18966_gb300", "csrc")
+    for f in os.listdir(csrc):
+        text = open(os.path.join(csrc, f)).read()
+        assert "oracle/" not in text and "svds_oracle" not in text and "orc_" not in text
+    pkg_init = open(os.path.join(ROOT, "paper_2405_18966_gb300", "__init__.py")).read()
+    assert "import oracle" not in pkg_init
