@@ -87,9 +87,21 @@ typedef struct svdsc_matrix {
  */
 typedef struct svdsc_options {
     int32_t precision;
-    int32_t reserved;
+    int32_t timing;     /* 1: time every kernel launch with CUDA events (fills svdsc_info.ms) */
     uint64_t seed;
 } svdsc_options;
+
+/* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
+enum svdsc_phase {
+    SVDSC_PH_SPMV = 0,     /* products with A and A^T (Alg. 1 lines 2, 5, 7) */
+    SVDSC_PH_GEMV_T = 1,   /* CGS projections h = W^T w */
+    SVDSC_PH_GEMV_N = 2,   /* CGS updates w -= W h */
+    SVDSC_PH_VEC = 3,      /* ordered reductions, norms, scaling (finalize) */
+    SVDSC_PH_SVD = 4,      /* projected SVD (Alg. 2 line 4) */
+    SVDSC_PH_GEMM = 5,     /* restart / output basis update (Alg. 2 lines 8, 15) */
+    SVDSC_PH_OTHER = 6,    /* residual test, T rebuild, sign rule, copies */
+    SVDSC_NUM_PHASES = 8
+};
 
 /* Per-solve report (all fields written by svdsc_solve). */
 typedef struct svdsc_info {
@@ -104,6 +116,17 @@ typedef struct svdsc_info {
     double beta_t;         /* T(t, t+1) of the last projected matrix */
     int32_t t;             /* subspace dimension used */
     int32_t reserved;
+    /* Per phase (index: enum svdsc_phase).  launches, algorithmic bytes and
+     * flops are always counted; ms only when the context was created with
+     * timing = 1 (summed CUDA-event durations of the launches).  Algorithmic
+     * bytes count each operand once: CSR SpMV 12 nnz + 20 rows + 8 cols (+8 rows
+     * for the fused axpy), FP32 form 8 nnz + ...; GEMV-T 8 len ncols + 8 len;
+     * GEMV-N 8 len ncols + 16 len (FP32 shadow: 4 len ncols instead of 8);
+     * restart GEMM 8 rows (t + k). */
+    double ms[SVDSC_NUM_PHASES];
+    int64_t launches[SVDSC_NUM_PHASES];
+    double bytes[SVDSC_NUM_PHASES];
+    double flops[SVDSC_NUM_PHASES];
 } svdsc_info;
 
 typedef struct svdsc_ctx svdsc_ctx;

@@ -43,17 +43,28 @@ class SvdscMatrix(C.Structure):
 
 
 class SvdscOptions(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
+    _fields_ = [("precision", C.c_int32), ("timing", C.c_int32), ("seed", C.c_uint64)]
+
+
+NUM_PHASES = 8
+PHASES = ("spmv", "gemv_t", "gemv_n", "vec", "svd", "gemm", "other", "unused")
 
 
 class SvdscInfo(C.Structure):
     _fields_ = [("converged", C.c_int32), ("nconv", C.c_int32), ("restarts", C.c_int32),
                 ("breakdowns", C.c_int32), ("n_matvec", C.c_int64), ("n_steps", C.c_int64),
                 ("n_launches", C.c_int64), ("anorm_est", C.c_double), ("beta_t", C.c_double),
-                ("t", C.c_int32), ("reserved", C.c_int32)]
+                ("t", C.c_int32), ("reserved", C.c_int32),
+                ("ms", C.c_double * NUM_PHASES), ("launches", C.c_int64 * NUM_PHASES),
+                ("bytes", C.c_double * NUM_PHASES), ("flops", C.c_double * NUM_PHASES)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d = {f: getattr(self, f) for f, _ in self._fields_
+             if f not in ("reserved", "ms", "launches", "bytes", "flops")}
+        for f in ("ms", "launches", "bytes", "flops"):
+            arr = getattr(self, f)
+            d[f] = {PHASES[i]: arr[i] for i in range(NUM_PHASES - 1)}
+        return d
 
 
 _lib = None
@@ -122,7 +133,7 @@ class Result:
 class Solver:
     """A matrix prepared on the device (svdsc_create) that can be solved many times."""
 
-    def __init__(self, A, precision: str = "fp64", seed: int = 0, stream=None):
+    def __init__(self, A, precision: str = "fp64", seed: int = 0, stream=None, timing: bool = False):
         self._keep = []
         self.handle = C.c_void_p()
         prec = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -159,7 +170,7 @@ class Solver:
             mat.m, mat.n = a.shape[0], a.shape[1]
             mat.value_type = F64
             self.m, self.n = int(a.shape[0]), int(a.shape[1])
-        opt = SvdscOptions(prec, 0, seed)
+        opt = SvdscOptions(prec, int(timing), seed)
         st = None if stream is None else C.c_void_p(int(stream))
         self.stream = stream
         _check(lib().svdsc_create(C.byref(self.handle), C.byref(mat), C.byref(opt), st), "svdsc_create")

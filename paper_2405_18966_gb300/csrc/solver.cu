@@ -49,7 +49,59 @@ struct svdsc_ctx {
     int breakdowns = 0;
     int64_t n_matvec = 0, n_steps = 0;
     std::vector<StepRec> steps;
+    // per-phase accounting (svdsc_info.ms / launches / bytes / flops)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Rec { int ph, e0, e1; };
+    std::vector<Rec> recs;
+    int64_t ph_launch[SVDSC_NUM_PHASES] = {0};
+    double ph_bytes[SVDSC_NUM_PHASES] = {0};
+    double ph_flops[SVDSC_NUM_PHASES] = {0};
 };
+
+static int next_event(svdsc_ctx *c)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        c->ev_pool.push_back(e);
+    }
+    return (int)c->ev_used++;
+}
+
+// Opens a timed region on the stream (returns -1 when timing is off).
+static int ph_begin(svdsc_ctx *c)
+{
+    if (!c->timing) return -1;
+    const int e = next_event(c);
+    if (e >= 0) cudaEventRecord(c->ev_pool[e], c->stream);
+    return e;
+}
+
+static void ph_end(svdsc_ctx *c, int ph, int e0, int nlaunch, double bytes, double flops)
+{
+    c->ph_launch[ph] += nlaunch;
+    c->ph_bytes[ph] += bytes;
+    c->ph_flops[ph] += flops;
+    c->launches += nlaunch;
+    if (e0 < 0) return;
+    const int e1 = next_event(c);
+    if (e1 < 0) return;
+    cudaEventRecord(c->ev_pool[e1], c->stream);
+    c->recs.push_back({ph, e0, e1});
+}
+
+static void ph_reset(svdsc_ctx *c)
+{
+    c->ev_used = 0;
+    c->recs.clear();
+    for (int i = 0; i < SVDSC_NUM_PHASES; i++) {
+        c->ph_launch[i] = 0;
+        c->ph_bytes[i] = 0.0;
+        c->ph_flops[i] = 0.0;
+    }
+}
 
 #define CU(x)                                          \
     do {                                               \
@@ -178,9 +230,10 @@ static int gemm_inplace(svdsc_ctx *c, double *W, int64_t ld, int64_t rows, int t
         attr = 200 * 1024;
     }
     const int64_t blocks = std::min<int64_t>((rows + 31) / 32, 152 * (smem > 100 * 1024 ? 1 : 2));
+    const int e0 = ph_begin(c);
     gemm_inplace_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), kGemmGroups * 32, smem, c->stream>>>(
         W, ld, rows, t, Q, t, k, KC);
-    c->launches++;
+    ph_end(c, SVDSC_PH_GEMM, e0, 1, 8.0 * rows * (t + k), 2.0 * rows * t * k);
     CU(cudaGetLastError());
     return SVDSC_OK;
 }
@@ -315,19 +368,47 @@ static int apply_A(svdsc_ctx *c, int trans, const double *x, const float *x32, c
                    const double *coef_dev, double coef_h, double *y, const int *poison)
 {
     cudaError_t e;
+    const int e0 = ph_begin(c);
+    int nl = 1;
+    double bytes, flops;
     if (c->format == SVDSC_CSR) {
         const DevCSR &M = trans ? c->AT : c->A;
-        if (c->precision == SVDSC_MIXED) e = csr_spmv_f32(M, x32, z, coef_dev, coef_h, y, poison, c->stream);
+        const bool f32 = c->precision == SVDSC_MIXED;
+        if (f32) e = csr_spmv_f32(M, x32, z, coef_dev, coef_h, y, poison, c->stream);
         else e = csr_spmv_f64(M, x, z, coef_dev, coef_h, y, poison, c->stream);
-        c->launches++;
+        bytes = (f32 ? 8.0 : 12.0) * M.nnz + 20.0 * M.m + (f32 ? 4.0 : 8.0) * M.n + (z ? 8.0 * M.m : 0.0);
+        flops = 2.0 * M.nnz;
     } else {
-        int l = 0;
-        if (trans) e = dense_gemv_t(c->D, x, z, coef_dev, coef_h, y, c->dense_part, poison, c->stream, &l);
-        else e = dense_gemv_n(c->D, x, z, coef_dev, coef_h, y, c->dense_part, poison, c->stream, &l);
-        c->launches += l;
+        nl = 0;
+        if (trans) e = dense_gemv_t(c->D, x, z, coef_dev, coef_h, y, c->dense_part, poison, c->stream, &nl);
+        else e = dense_gemv_n(c->D, x, z, coef_dev, coef_h, y, c->dense_part, poison, c->stream, &nl);
+        const double out = trans ? c->D.n : c->D.m, in = trans ? c->D.m : c->D.n;
+        bytes = 8.0 * c->D.m * c->D.n + 8.0 * in + 8.0 * out + (z ? 8.0 * out : 0.0);
+        flops = 2.0 * c->D.m * c->D.n;
     }
+    ph_end(c, SVDSC_PH_SPMV, e0, nl, bytes, flops);
     c->n_matvec++;
     return e == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
+}
+
+// One CGS pass: h = W^T w, then w -= W h (Pn: partial sums of the new ||w||^2).
+static void cgs_pass(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, int ncols, double *w,
+                     const Chunk &ch, double *Pn, const int *poison)
+{
+    cudaStream_t s = c->stream;
+    const double L = (double)ch.len, nc = ncols;
+    const double wsz = W32 ? 4.0 : 8.0;
+    int e0 = ph_begin(c);
+    if (W32) proj_partial_f32(W32, ld, ncols, w, ch, c->P, poison, s);
+    else proj_partial(W, ld, ncols, w, ch, c->P, poison, s);
+    ph_end(c, SVDSC_PH_GEMV_T, e0, 1, wsz * L * nc + 8.0 * L, 2.0 * L * nc);
+    e0 = ph_begin(c);
+    proj_reduce(c->P, ch.nb, ncols, c->h, poison, s);
+    ph_end(c, SVDSC_PH_VEC, e0, 1, 8.0 * ch.nb * nc, ch.nb * nc);
+    e0 = ph_begin(c);
+    if (W32) update_sub_f32(W32, ld, ncols, c->h, w, ch, poison, s);
+    else update_sub(W, ld, ncols, c->h, w, ch, Pn, poison, s);
+    ph_end(c, SVDSC_PH_GEMV_N, e0, 1, wsz * L * nc + 16.0 * L, 2.0 * L * nc);
 }
 
 // CGS2: w <- (I - W W^T)^2 w against ncols columns; leaves the partial sums
@@ -335,24 +416,13 @@ static int apply_A(svdsc_ctx *c, int trans, const double *x, const float *x32, c
 static void cgs2(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, int ncols, double *w,
                  const Chunk &ch, const int *poison)
 {
-    cudaStream_t s = c->stream;
     if (ncols > 0) {
-        if (W32) {
-            proj_partial_f32(W32, ld, ncols, w, ch, c->P, poison, s);
-            proj_reduce(c->P, ch.nb, ncols, c->h, poison, s);
-            update_sub_f32(W32, ld, ncols, c->h, w, ch, poison, s);
-        } else {
-            proj_partial(W, ld, ncols, w, ch, c->P, poison, s);
-            proj_reduce(c->P, ch.nb, ncols, c->h, poison, s);
-            update_sub(W, ld, ncols, c->h, w, ch, nullptr, poison, s);
-        }
-        proj_partial(W, ld, ncols, w, ch, c->P, poison, s);
-        proj_reduce(c->P, ch.nb, ncols, c->h, poison, s);
-        update_sub(W, ld, ncols, c->h, w, ch, c->Pn, poison, s);
-        c->launches += 6;
+        cgs_pass(c, W, W32, ld, ncols, w, ch, nullptr, poison);
+        cgs_pass(c, W, nullptr, ld, ncols, w, ch, c->Pn, poison);
     } else {
-        norm_partial(w, ch, c->Pn, poison, s);
-        c->launches += 1;
+        const int e0 = ph_begin(c);
+        norm_partial(w, ch, c->Pn, poison, c->stream);
+        ph_end(c, SVDSC_PH_VEC, e0, 1, 8.0 * ch.len, 2.0 * ch.len);
     }
 }
 
@@ -363,9 +433,10 @@ static void do_finalize(svdsc_ctx *c, int side, int col, double *T_entry, int mo
     float *w32 = side == 0 ? colU32(c, col) : colV32(c, col);
     const int step = (int)c->steps.size();
     c->steps.push_back({side, col, c->parity});
+    const int e0 = ph_begin(c);
     finalize(w, ch, c->Pn, T_entry, c->st, step, c->parity, mode, w32, c->stream);
+    ph_end(c, SVDSC_PH_VEC, e0, 1, (w32 ? 20.0 : 16.0) * ch.len, ch.len);
     c->parity ^= 1;
-    c->launches++;
     c->n_steps++;
 }
 
@@ -444,7 +515,7 @@ static int settle(svdsc_ctx *c)
             double *w = rec.side == 0 ? colU(c, rec.col) : colV(c, rec.col);
             const Chunk &ch = rec.side == 0 ? c->cm : c->cn;
             rng_normal_vec(c->seed, c->draws++, ch.len, w, c->stream);
-            c->launches++;
+            ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0);
             if (rec.side == 0) cgs2(c, c->U, nullptr, c->ldu, rec.col, w, ch, poison_ptr(c));
             else cgs2(c, c->V, nullptr, c->ldv, rec.col, w, ch, poison_ptr(c));
             double *Te = nullptr;
@@ -499,6 +570,7 @@ int svdsc_destroy(svdsc_ctx *c)
     cudaFree(c->dense_part);
     cudaFree(c->st);
     cudaFreeHost(c->st_host);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return SVDSC_OK;
 }
@@ -526,6 +598,7 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
     c->stream = (cudaStream_t)stream;
     c->precision = prec;
     c->seed = opt ? opt->seed : 0;
+    c->timing = opt ? (opt->timing != 0) : false;
     c->format = A->format;
     c->m = A->m;
     c->n = A->n;
@@ -600,6 +673,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     c->t = t;
     c->k = k;
     c->launches = 0;
+    ph_reset(c);
     c->parity = 0;
     c->draws = 0;
     c->breakdowns = 0;
@@ -619,10 +693,10 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     // Alg. 1 line 1: v_1 (the caller's v0 or draw 0), normalised
     if (v0) CU(cudaMemcpyAsync(colV(c, 0), v0, sizeof(double) * c->n,
                                v0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    else { rng_normal_vec(c->seed, 0, c->n, colV(c, 0), s); c->launches++; }
+    else { rng_normal_vec(c->seed, 0, c->n, colV(c, 0), s); ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0); }
     c->draws = 1;
     norm_partial(colV(c, 0), c->cn, c->Pn, nullptr, s);
-    c->launches++;
+    ph_end(c, SVDSC_PH_VEC, -1, 1, 8.0 * c->n, 2.0 * c->n);
     do_finalize(c, 1, 0, nullptr, 1);
     rc = read_status(c);
     if (rc) return rc;
@@ -635,7 +709,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         c->parity = 0;
         rng_normal_vec(c->seed, c->draws++, c->n, colV(c, 0), s);
         norm_partial(colV(c, 0), c->cn, c->Pn, nullptr, s);
-        c->launches += 2;
+        ph_end(c, SVDSC_PH_OTHER, -1, 2, 0.0, 0.0);
         do_finalize(c, 1, 0, nullptr, 1);
     }
     c->steps.clear();   // step ids below index Lanczos vectors only
@@ -644,7 +718,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     rc = apply_A(c, 0, colV(c, 0), colV32(c, 0), nullptr, nullptr, 0.0, colU(c, 0), poison_ptr(c));
     if (rc) return rc;
     norm_partial(colU(c, 0), c->cm, c->Pn, poison_ptr(c), s);
-    c->launches++;
+    ph_end(c, SVDSC_PH_VEC, -1, 1, 8.0 * c->m, 2.0 * c->m);
     do_finalize(c, 0, 0, Tent(c, 0, 0), 0);
     // Alg. 2 line 2: LBP(A, t+1)
     rc = issue_segment(c, 1, false);
@@ -655,11 +729,17 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     int restarts = 0;
     for (int it = 1; it <= maxit; it++) {
         // line 4: SVD of T(1:t,1:t)
-        CU(small_svd(t, c->T, t + 1, c->Sh, c->Uh, c->Vh, c->svd, c->st, s, nullptr));
-        c->launches++;
+        {
+            const int e0 = ph_begin(c);
+            CU(small_svd(t, c->T, t + 1, c->Sh, c->Uh, c->Vh, c->svd, c->st, s, nullptr));
+            ph_end(c, SVDSC_PH_SVD, e0, 1, 0.0, 0.0);
+        }
         // line 5: residual test (Eq. 4)
-        residual_kernel<<<1, 256, 0, s>>>(t, k, tol, c->T, c->Sh, c->Uh, c->res, c->rho, c->st, c->parity);
-        c->launches++;
+        {
+            const int e0 = ph_begin(c);
+            residual_kernel<<<1, 256, 0, s>>>(t, k, tol, c->T, c->Sh, c->Uh, c->res, c->rho, c->st, c->parity);
+            ph_end(c, SVDSC_PH_OTHER, e0, 1, 0.0, 0.0);
+        }
         CU(cudaGetLastError());
         rc = read_status(c);
         if (rc) return rc;
@@ -674,16 +754,19 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         if (c->precision == SVDSC_MIXED) {
             copy_f64_to_f32(c->U, c->U32, c->ldu * k, s);
             copy_f64_to_f32(c->V, c->V32, c->ldv * (k + 1), s);
-            c->launches += 2;
+            ph_end(c, SVDSC_PH_OTHER, -1, 2, 12.0 * (c->ldu * k + c->ldv * (k + 1)), 0.0);
         }
         restart_T_kernel<<<1, 256, 0, s>>>(t, k, c->T, c->Sh, c->rho);
-        c->launches++;
+        ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0);
         CU(cudaGetLastError());
         // u_{k+1} = A v_{k+1} - U~_k rho (Eq. 7), re-orthogonalized against U~_k
         rc = apply_A(c, 0, colV(c, k), colV32(c, k), nullptr, nullptr, 0.0, colU(c, k), poison_ptr(c));
         if (rc) return rc;
-        update_sub(c->U, c->ldu, k, c->rho, colU(c, k), c->cm, nullptr, poison_ptr(c), s);
-        c->launches++;
+        {
+            const int e0 = ph_begin(c);
+            update_sub(c->U, c->ldu, k, c->rho, colU(c, k), c->cm, nullptr, poison_ptr(c), s);
+            ph_end(c, SVDSC_PH_GEMV_N, e0, 1, 8.0 * c->m * k + 16.0 * c->m, 2.0 * c->m * k);
+        }
         cgs2(c, c->U, c->U32, c->ldu, k, colU(c, k), c->cm, poison_ptr(c));
         do_finalize(c, 0, k, Tent(c, k, k), 0);
         restarts++;
@@ -701,7 +784,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     rc = gemm_inplace(c, c->V, c->ldv, c->n, t, c->Vh, k);
     if (rc) return rc;
     sign_kernel<<<k, 256, 0, s>>>(c->U, c->ldu, c->m, c->V, c->ldv, c->n);
-    c->launches++;
+    ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0);
     CU(cudaGetLastError());
     const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CU(cudaMemcpyAsync(S, c->Sh, sizeof(double) * k, kind, s));
@@ -723,6 +806,16 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         info->anorm_est = std::max(fin.anorm[0], fin.anorm[1]);
         info->beta_t = fin.beta_t;
         info->t = t;
+        for (int i = 0; i < SVDSC_NUM_PHASES; i++) {
+            info->launches[i] = c->ph_launch[i];
+            info->bytes[i] = c->ph_bytes[i];
+            info->flops[i] = c->ph_flops[i];
+        }
+        for (const auto &r : c->recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->ev_pool[r.e0], c->ev_pool[r.e1]) == cudaSuccess)
+                info->ms[r.ph] += ms;
+        }
     }
     return fin.converged ? SVDSC_OK : SVDSC_NOT_CONVERGED;
 }

@@ -56,7 +56,8 @@ template <typename VT, typename XT, typename AT>
 __global__ void __launch_bounds__(kSpmvThreads)
 csr_spmv_binned(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                 const VT *__restrict__ val, const XT *__restrict__ x,
-                const int32_t *__restrict__ perm, Bins bins, const double *__restrict__ z,
+                const int32_t *__restrict__ perm, const __grid_constant__ Bins bins,
+                const double *__restrict__ z,
                 const double *__restrict__ coef_dev, double coef_h, double *__restrict__ y,
                 const int *poison)
 {
