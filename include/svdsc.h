@@ -206,6 +206,32 @@ int svdsc_small_svd(svdsc_ctx *ctx, int t, const double *T, int64_t ldt, double 
  * itself; the component entry points need it first). */
 int svdsc_reserve(svdsc_ctx *ctx, int t);
 
+/*
+ * The same CGS2 as svdsc_cgs2 (w <- (I - W W^T)^2 w, then *norm_out = ||w||_2),
+ * for callers that cannot allocate device memory: no context, and no
+ * cudaMalloc, cudaFree or allocating library call at any point.  Callers of
+ * this kind include code running while a framework's caching allocator holds
+ * all device memory, serving or real-time loops with a memory budget fixed up
+ * front (cudaMalloc can synchronize the device and can fail mid-run), and
+ * hosts that only hand a library pre-allocated buffers.  The paper has no
+ * counterpart; it exists only for such callers.
+ *   Scratch: one file-scope __device__ array of 4.2 MB (525,824 doubles) that
+ *   every GPU loading this library holds until the process exits.  Limits:
+ *   ncols <= 512 and len <= 4,194,304 (at most 1,024 row chunks of 4,096);
+ *   larger sizes return SVDSC_ERR_SIZE before any GPU work.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.  Every call shares the array and overwrites
+ *   what it reads, so calls whose GPU work overlaps (two streams, two host
+ *   threads) race and give wrong results; serialize them.
+ *   W (len x ncols, leading dimension ldw, even, 16-byte aligned), w (len,
+ *   16-byte aligned, overwritten), norm_out (one double): device pointers.
+ *   stream: cudaStream_t or NULL.  The call only enqueues the work on stream
+ *   and returns; results are ready once the stream reaches it.
+ */
+int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, int64_t ldw, double *w,
+                       double *norm_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

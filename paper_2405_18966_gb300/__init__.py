@@ -31,7 +31,7 @@ F64, F32 = 0, 1
 
 # Every symbol include/svdsc.h declares.
 EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "svdsc_matvec",
-           "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve")
+           "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc")
 
 
 class SvdscMatrix(C.Structure):
@@ -88,6 +88,7 @@ def lib():
         L.svdsc_cgs2.argtypes = [vp, i64, i64, vp, i64, vp, vp]
         L.svdsc_small_svd.argtypes = [vp, i32, vp, i64, vp, vp, vp]
         L.svdsc_reserve.argtypes = [vp, i32]
+        L.svdsc_cgs2_noalloc.argtypes = [i64, i64, vp, i64, vp, vp, vp]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or C.c_int
         L.svdsc_strerror.restype = C.c_char_p
