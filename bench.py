@@ -272,6 +272,63 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def run_kernel(args):
+    """A few launches of one component on the Zipf workload's shapes (profiling aid)."""
+    import torch
+    import paper_2405_18966_gb300 as pkg
+    from paper_2405_18966_gb300 import build as _build
+    _build.build()
+    A, k, p, tol, prec = make_workload(args.workload, args.scale)
+    s = pkg.Solver(A, precision=prec, timing=False)
+    m, n = A.m, A.n
+    g = torch.Generator(device="cuda").manual_seed(0)
+    res = {}
+    if args.kernel in ("spmv", "spmv_t"):
+        tr = args.kernel == "spmv_t"
+        x = torch.randn(m if tr else n, dtype=torch.float64, device="cuda", generator=g)
+        fn = lambda: s.matvec(x, trans=tr)
+        nbytes = 12.0 * A.nnz + 20.0 * (n if tr else m) + 8.0 * (m if tr else n)
+    elif args.kernel == "cgs2":
+        s.reserve(args.ncols + 2)
+        Wt = torch.randn((args.ncols, m), dtype=torch.float64, device="cuda", generator=g) / np.sqrt(m)
+        w = torch.randn(m, dtype=torch.float64, device="cuda", generator=g)
+        fn = lambda: s.cgs2(Wt, w)
+        nbytes = 2 * (8.0 * m * args.ncols * 2 + 24.0 * m)
+    elif args.kernel == "small_svd":
+        t = args.ncols
+        s.reserve(t)
+        T = torch.triu(torch.randn((t, t), dtype=torch.float64, device="cuda", generator=g))
+        fn = lambda: s.small_svd(T)
+        nbytes = 0.0
+    else:
+        import ctypes as C
+        t = args.ncols
+        s.reserve(t)
+        Wc = torch.randn((t, m), dtype=torch.float64, device="cuda", generator=g) / np.sqrt(m)  # column-major m x t
+        Qc = torch.linalg.qr(torch.randn((t, t), dtype=torch.float64, device="cuda", generator=g))[0][:k, :]
+        Qc = Qc.contiguous()  # column-major t x k (rows of Qc are columns)
+        Cc = torch.empty((k, m), dtype=torch.float64, device="cuda")
+        mode = 1 if args.kernel == "gemm_mixed" else 0
+        L = pkg.lib()
+        fn = lambda: L.svdsc_gemm(s.handle, mode, m, t, k, C.c_void_p(Wc.data_ptr()), m,
+                                  C.c_void_p(Qc.data_ptr()), t, C.c_void_p(Cc.data_ptr()), m)
+        nbytes = 8.0 * m * t + 8.0 * m * k
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    res = {"kernel": args.kernel, "workload": args.workload, "scale": args.scale, "m": m, "n": n,
+           "ncols": args.ncols, "ms_per_call": ms, "alg_GBps": (nbytes / (ms * 1e-3) / 1e9) if nbytes else None}
+    print(json.dumps(res), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -284,10 +341,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--ref-restarts", type=int, default=10)
+    ap.add_argument("--kernel", choices=["spmv", "spmv_t", "cgs2", "gemm", "gemm_mixed", "small_svd"],
+                    help="time a few launches of one hot-path step through its component entry point "
+                         "(for profiling) instead of whole solves")
+    ap.add_argument("--ncols", type=int, default=150, help="basis columns for --kernel cgs2 / gemm t")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.kernel:
+        return run_kernel(args)
 
     import torch
     torch.cuda.set_device(local)

@@ -87,8 +87,10 @@ typedef struct svdsc_matrix {
  */
 typedef struct svdsc_options {
     int32_t precision;
-    int32_t timing;     /* 1: time every kernel launch with CUDA events (fills svdsc_info.ms) */
+    int32_t timing;        /* 1: time every kernel launch with CUDA events (fills svdsc_info.ms) */
     uint64_t seed;
+    int32_t restart_gemm;  /* 0: tensor cores (svdsc_gemm modes 0/1, default); 1: FP64 FMA on CUDA cores */
+    int32_t reserved;
 } svdsc_options;
 
 /* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
@@ -205,6 +207,25 @@ int svdsc_small_svd(svdsc_ctx *ctx, int t, const double *T, int64_t ldt, double 
 /* Sizes the context's workspace for subspace dimension t (solve does this
  * itself; the component entry points need it first). */
 int svdsc_reserve(svdsc_ctx *ctx, int t);
+
+/*
+ * Restart / output basis update of Alg. 2 lines 8 and 15 on the tensor cores:
+ * C = W Q with W rows x t (leading dimension ldw), Q t x k (ldq), C rows x k
+ * (ldc), all column-major FP64 device arrays; C must not overlap W.
+ *   mode 0 (FP64 form): both operands are cut into nine signed 6-bit digit
+ *   slices on power-of-two row / column scales (an Ozaki-style error-free
+ *   split), the 45 slice products run as BF16 tcgen05 MMAs whose FP32
+ *   accumulations are exact integers, and the epilogue recombines them
+ *   exactly before one FP64 rounding: accuracy of an FP64 GEMM (needs
+ *   t <= 448).
+ *   mode 1 (mixed form): W rounded to FP32 and Q are cut into three BF16 pieces
+ *   each; the six leading piece products accumulate in FP32 (about FP32
+ *   accuracy).
+ * Needs t <= t_max of the context (svdsc_reserve) and k <= t.  Runs on the
+ * context's stream and synchronizes it.
+ */
+int svdsc_gemm(svdsc_ctx *ctx, int mode, int64_t rows, int t, int k, const double *W, int64_t ldw,
+               const double *Q, int64_t ldq, double *C, int64_t ldc);
 
 /*
  * The same CGS2 as svdsc_cgs2 (w <- (I - W W^T)^2 w, then *norm_out = ||w||_2),

@@ -31,7 +31,8 @@ F64, F32 = 0, 1
 
 # Every symbol include/svdsc.h declares.
 EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "svdsc_matvec",
-           "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc")
+           "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc",
+           "svdsc_gemm")
 
 
 class SvdscMatrix(C.Structure):
@@ -43,7 +44,8 @@ class SvdscMatrix(C.Structure):
 
 
 class SvdscOptions(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("timing", C.c_int32), ("seed", C.c_uint64)]
+    _fields_ = [("precision", C.c_int32), ("timing", C.c_int32), ("seed", C.c_uint64),
+                ("restart_gemm", C.c_int32), ("reserved", C.c_int32)]
 
 
 NUM_PHASES = 8
@@ -89,6 +91,7 @@ def lib():
         L.svdsc_small_svd.argtypes = [vp, i32, vp, i64, vp, vp, vp]
         L.svdsc_reserve.argtypes = [vp, i32]
         L.svdsc_cgs2_noalloc.argtypes = [i64, i64, vp, i64, vp, vp, vp]
+        L.svdsc_gemm.argtypes = [vp, i32, i64, i32, i32, vp, i64, vp, i64, vp, i64]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or C.c_int
         L.svdsc_strerror.restype = C.c_char_p
@@ -134,7 +137,8 @@ class Result:
 class Solver:
     """A matrix prepared on the device (svdsc_create) that can be solved many times."""
 
-    def __init__(self, A, precision: str = "fp64", seed: int = 0, stream=None, timing: bool = False):
+    def __init__(self, A, precision: str = "fp64", seed: int = 0, stream=None, timing: bool = False,
+                 restart_gemm: str = "tensor"):
         self._keep = []
         self.handle = C.c_void_p()
         prec = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -171,7 +175,7 @@ class Solver:
             mat.m, mat.n = a.shape[0], a.shape[1]
             mat.value_type = F64
             self.m, self.n = int(a.shape[0]), int(a.shape[1])
-        opt = SvdscOptions(prec, int(timing), seed)
+        opt = SvdscOptions(prec, int(timing), seed, {"tensor": 0, "fma": 1}[restart_gemm], 0)
         st = None if stream is None else C.c_void_p(int(stream))
         self.stream = stream
         _check(lib().svdsc_create(C.byref(self.handle), C.byref(mat), C.byref(opt), st), "svdsc_create")
@@ -250,6 +254,18 @@ class Solver:
                "svdsc_cgs2")
         return w, float(nrm.item())
 
+    def gemm(self, W, Q, mode: int = 0):
+        """C = W Q on the tensor cores (W: rows x t, Q: t x k torch CUDA float64)."""
+        import torch
+        rows, t = W.shape
+        k = Q.shape[1]
+        Wc = W.t().contiguous()  # column-major storage
+        Qc = Q.t().contiguous()
+        Ct = torch.empty((k, rows), dtype=torch.float64, device=W.device)
+        _check(lib().svdsc_gemm(self.handle, mode, rows, t, k, _ptr(Wc), rows, _ptr(Qc), t, _ptr(Ct), rows),
+               "svdsc_gemm")
+        return Ct.t()
+
     def small_svd(self, T):
         """T: t x t torch CUDA float64 tensor; returns (S, Uh, Vh) with T = Uh diag(S) Vh^T."""
         import torch
@@ -264,7 +280,7 @@ class Solver:
 
 
 def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, precision: str = "fp64",
-         seed: int = 0, v0=None, out: str = "host") -> Result:
+         seed: int = 0, v0=None, out: str = "host", restart_gemm: str = "tensor") -> Result:
     """One-shot convenience: create, solve, destroy."""
-    with Solver(A, precision=precision, seed=seed) as s:
+    with Solver(A, precision=precision, seed=seed, restart_gemm=restart_gemm) as s:
         return s.solve(k, p, tol, maxit, v0=v0, out=out)

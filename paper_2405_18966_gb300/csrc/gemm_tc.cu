@@ -1,0 +1,495 @@
+// Restart / output basis update of Alg. 2 (lines 8 and 15 of the svds-C
+// paper): C (rows x k) = W (rows x t) Q (t x k), W tall and skinny, on the
+// 5th-generation tensor cores (tcgen05.mma, accumulators in TMEM).
+//
+// Operands are cut into BF16 "slices" and every slice pair with s + s' <= S + 1
+// is multiplied on the tensor cores with FP32 accumulation:
+//   * FP64 form (Ozaki-style error-free splitting, Ozaki et al. 2012): each row
+//     of W and each column of Q is scaled by a power of two, its fixed-point
+//     value is cut into S = 9 signed 6-bit digits (54 bits), and the 53 digit
+//     products with s + s' <= 11 are summed in 10 TMEM accumulators, one per
+//     digit weight d = s + s'.  Every accumulator holds an integer below 2^24
+//     (t <= 448), so the FP32 tensor-core sums are exact; the epilogue
+//     recombines the 10 integers exactly in int64 and rounds once to FP64.
+//     The dropped products (s + s' >= 12) bound the error by about
+//     2^-49 max|W(r,:)| max|Q(:,j)| (worst case; typically 2^-55).
+//   * mixed form: W (FP32 shadow) and Q are cut into 3 floating BF16 pieces
+//     (hi, mid, lo: 24 bits) and the 6 products with s + s' <= 4 accumulate in
+//     one FP32 accumulator.
+// A CTA owns 128 rows x NT columns of C; the K dimension (t) streams through a
+// two-stage shared-memory pipeline of 32-wide chunks: the CTA's threads cut the
+// next chunk into slices while the tensor cores multiply the current one.
+// C must not alias W (the caller ping-pongs two bases).
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include "internal.cuh"
+
+namespace svdsc {
+
+// ------------------------------------------------------------------ PTX
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^22 polls (each try_wait also suspends for a
+// hardware-chosen interval) and reports the timeout instead of hanging.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < (1u << 22); i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand without swizzling: core
+// matrices of 8 rows x 16 bytes stored contiguously (128 B); lbo = byte
+// distance between core matrices adjacent along K, sbo = along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ------------------------------------------------------------- geometry
+constexpr int kTM = 128;        // rows per CTA (MMA M)
+constexpr int kKC = 32;         // K chunk per pipeline stage
+constexpr int kThreads = 128;   // one thread per row of the tile
+constexpr int kMaxT = 448;      // exactness bound of the FP64 form
+
+template <int S, int NT>
+struct TileCfg {
+    static constexpr int a_slice_bytes = kTM * kKC * 2;          // 8 KB
+    static constexpr int b_slice_bytes = NT * kKC * 2;
+    static constexpr int a_bytes = S * a_slice_bytes;
+    static constexpr int b_bytes = S * b_slice_bytes;
+    static constexpr int stage_bytes = a_bytes + b_bytes;
+    static constexpr int smem_bytes = 2 * stage_bytes + 1024;    // + alignment slack
+};
+
+// byte offset of element (row, kk) inside one K-major no-swizzle slice of
+// `rows` rows and kKC columns: [kgroup][rowgroup][8 rows][8 elements]
+__host__ __device__ __forceinline__ int core_off(int row, int kk, int rows)
+{
+    return ((kk >> 3) * (rows >> 3) + (row >> 3)) * 128 + (row & 7) * 16 + (kk & 7) * 2;
+}
+
+// ------------------------------------------------------------ slicing
+// FP64 form: x = sum_{s=1..9} digit_s 2^(e - 6 s), digits signed with |digit| <= 63,
+// e = the row (or column) exponent with max |x| < 2^e.
+__device__ __forceinline__ int dexp_of(double v)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7FF);
+    return E == 0 ? -100000 : E - 1022;  // |v| < 2^(E-1022); zero/denormal ignored
+}
+
+__device__ __forceinline__ void ozaki_digits(double v, int e, float (&dig)[9])
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const float sg = (b >> 63) ? -1.f : 1.f;
+    uint64_t F = 0;
+    if (E != 0) {
+        const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = e - (E - 1022);   // >= 0
+        F = sh >= 54 ? 0ull : ((mant << 1) >> sh);  // |v| 2^(54 - e), < 2^54
+    }
+#pragma unroll
+    for (int s = 0; s < 9; s++) dig[s] = sg * (float)(int)((F >> (6 * (8 - s))) & 63u);
+}
+
+// mixed form: x = hi + mid + lo, each a BF16 number (24 significant bits)
+__device__ __forceinline__ void float_pieces(float x, float (&p)[3])
+{
+    const float h = __bfloat162float(__float2bfloat16_rn(x));
+    const float r1 = x - h;
+    const float m = __bfloat162float(__float2bfloat16_rn(r1));
+    const float r2 = r1 - m;
+    p[0] = h;
+    p[1] = m;
+    p[2] = __bfloat162float(__float2bfloat16_rn(r2));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const uint32_t lo = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a));
+    const uint32_t hi = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b));
+    return lo | (hi << 16);
+}
+
+// ------------------------------------------------------------- B prep
+// Q (t x k, FP64) -> slices in the exact shared-memory layout each CTA copies:
+// Bs[(cb * nchunks + chunk) * S + s][NT x kKC core layout]; column exponents fexp[k].
+template <int S, int NT, bool OZAKI>
+__global__ void prep_b_kernel(const double *__restrict__ Q, int64_t ldq, int t, int k, int nchunks,
+                              int ncb, uint16_t *__restrict__ Bs, int *__restrict__ fexp)
+{
+    // one thread per (column j of the padded column space, chunk)
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.y;
+    if (j >= ncb * NT) return;
+    const int cb = j / NT, jn = j % NT;
+    int e = -100000;
+    if (OZAKI && j < k)
+        for (int c = 0; c < t; c++) e = max(e, dexp_of(Q[c + (int64_t)j * ldq]));
+    if (OZAKI && chunk == 0 && j < k) fexp[j] = e;
+    for (int kk = 0; kk < kKC; kk++) {
+        const int c = chunk * kKC + kk;
+        const double q = (j < k && c < t) ? Q[c + (int64_t)j * ldq] : 0.0;
+        float pieces[S];
+        if constexpr (OZAKI) {
+            float d9[9];
+            ozaki_digits(q, e, d9);
+#pragma unroll
+            for (int s = 0; s < S; s++) pieces[s] = d9[s];
+        } else {
+            float p3[3];
+            float_pieces((float)q, p3);
+#pragma unroll
+            for (int s = 0; s < S; s++) pieces[s] = p3[s];
+        }
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            uint16_t *dst = Bs + ((int64_t)(cb * nchunks + chunk) * S + s) * (NT * kKC);
+            dst[core_off(jn, kk, NT) / 2] = __bfloat16_as_ushort(__float2bfloat16_rn(pieces[s]));
+        }
+    }
+}
+
+// ------------------------------------------------------------- main kernel
+// G accumulators of NT columns: OZAKI -> one per digit weight d = s+s' (G = 9),
+// else a single one.  C = W Q for rows [128 bx, +128) and columns [NT by, +NT).
+template <int S, int NT, bool OZAKI, typename WT>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k,
+               const uint16_t *__restrict__ Bs, const int *__restrict__ fexp, int nchunks,
+               double *__restrict__ C, int64_t ldc, float *__restrict__ C32, int *err)
+{
+    constexpr int G = OZAKI ? 10 : 1;           // accumulators
+    constexpr int kMaxSum = OZAKI ? 9 : S - 1;  // kept pairs: s + s2 <= kMaxSum (0-based)
+    constexpr uint32_t kTmemCols = (G * NT <= 32) ? 32 : (G * NT <= 64) ? 64 : (G * NT <= 128) ? 128
+                                   : (G * NT <= 256) ? 256 : 512;
+    static_assert(G * NT <= 512, "TMEM capacity");
+    using Cfg = TileCfg<S, NT>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t mma_done[2];
+    __shared__ uint32_t tmem_base_slot;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t row0 = (int64_t)blockIdx.x * kTM;
+    const int cb = blockIdx.y;
+    const int64_t r = row0 + tid;
+    const bool row_ok = r < rows;
+
+    if (tid == 0) {
+        mbar_init(&mma_done[0], 1);
+        mbar_init(&mma_done[1], 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_slot;
+
+    // row exponent (FP64 form)
+    int e_r = -100000;
+    if (OZAKI && row_ok)
+        for (int c = 0; c < t; c++) e_r = max(e_r, dexp_of((double)W[r + (int64_t)c * ldw]));
+
+    uint32_t parity[2] = {0u, 0u};
+    bool used[2] = {false, false};
+    bool ok = true;
+    for (int chunk = 0; chunk < nchunks; chunk++) {
+        const int st = chunk & 1;
+        uint8_t *A = smem + st * Cfg::stage_bytes;
+        uint8_t *B = A + Cfg::a_bytes;
+        if (used[st]) {  // the MMAs that read this stage two chunks ago must be done
+            if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
+            parity[st] ^= 1u;
+        }
+        tc_fence_after();
+        // B slices for (cb, chunk): contiguous, copied as 16-byte words
+        {
+            const uint4 *src = (const uint4 *)(Bs + (int64_t)(cb * nchunks + chunk) * S * (NT * kKC));
+            uint4 *dst = (uint4 *)B;
+            for (int i = tid; i < Cfg::b_bytes / 16; i += kThreads) dst[i] = src[i];
+        }
+        // A slices: this thread's row, 4 groups of 8 consecutive K entries
+#pragma unroll
+        for (int kg = 0; kg < kKC / 8; kg++) {
+            float pc[S][8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int c = chunk * kKC + kg * 8 + q;
+                const double v = (row_ok && c < t) ? (double)W[r + (int64_t)c * ldw] : 0.0;
+                if constexpr (OZAKI) {
+                    float d9[9];
+                    ozaki_digits(v, e_r, d9);
+#pragma unroll
+                    for (int s = 0; s < S; s++) pc[s][q] = d9[s];
+                } else {
+                    float p3[3];
+                    float_pieces((float)v, p3);
+#pragma unroll
+                    for (int s = 0; s < S; s++) pc[s][q] = p3[s];
+                }
+            }
+            const int off = core_off(tid, kg * 8, kTM);
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                uint4 w4;
+                w4.x = pack_bf16(pc[s][0], pc[s][1]);
+                w4.y = pack_bf16(pc[s][2], pc[s][3]);
+                w4.z = pack_bf16(pc[s][4], pc[s][5]);
+                w4.w = pack_bf16(pc[s][6], pc[s][7]);
+                *(uint4 *)(A + s * Cfg::a_slice_bytes + off) = w4;
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            constexpr uint32_t idesc = idesc_bf16(kTM, NT);
+            const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+            constexpr uint32_t a_lbo = (kTM / 8) * 128, a_sbo = 128;
+            constexpr uint32_t b_lbo = (NT / 8) * 128, b_sbo = 128;
+#pragma unroll
+            for (int ks = 0; ks < kKC / 16; ks++) {
+#pragma unroll
+                for (int s = 0; s < S; s++) {
+#pragma unroll
+                    for (int s2 = 0; s2 < S; s2++) {
+                        if (s + s2 > kMaxSum) continue;
+                        const int g = OZAKI ? (s + s2) : 0;
+                        const uint64_t ad = smem_desc(a0 + s * Cfg::a_slice_bytes + ks * 2 * a_lbo, a_lbo, a_sbo);
+                        const uint64_t bd = smem_desc(b0 + s2 * Cfg::b_slice_bytes + ks * 2 * b_lbo, b_lbo, b_sbo);
+                        // the first product into each accumulator overwrites it:
+                        // group g = s + s2 is first reached at s = max(0, g - (S - 1))
+                        const int s_first = (OZAKI && g > S - 1) ? g - (S - 1) : 0;
+                        const bool first = chunk == 0 && ks == 0 && s == s_first && (OZAKI || s2 == 0);
+                        umma_bf16(tmem + (uint32_t)(g * NT), ad, bd, idesc, first ? 0u : 1u);
+                    }
+                }
+            }
+            umma_commit(&mma_done[st]);
+        }
+        used[st] = true;
+    }
+    // wait for the last commits of both stages
+    for (int st = 0; st < 2; st++)
+        if (used[st]) {
+            if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
+            parity[st] ^= 1u;
+        }
+    tc_fence_after();
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows 32w..32w+31
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const int j0 = cb * NT;
+        for (int c8 = 0; c8 < NT; c8 += 8) {
+            if (j0 + c8 >= k) break;
+            double out[8];
+            if constexpr (OZAKI) {
+                // X_d (d = g + 2) are exact integers; Horner in three exact
+                // int64 groups: d = 2..5, 6..8, 9..11
+                long long zh[8], zm[8], zl[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) { zh[q] = 0; zm[q] = 0; zl[q] = 0; }
+#pragma unroll
+                for (int g = 0; g < G; g++) {
+                    uint32_t x[8];
+                    tmem_ld8(tmem + lane_base + (uint32_t)(g * NT + c8), x);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const long long xi = (long long)__float2int_rn(__uint_as_float(x[q]));
+                        if (g < 4) zh[q] = zh[q] * 64 + xi;
+                        else if (g < 7) zm[q] = zm[q] * 64 + xi;
+                        else zl[q] = zl[q] * 64 + xi;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int j = j0 + c8 + q;
+                    const int ef = (j < k) ? fexp[j] : 0;
+                    const double v = fma((double)zh[q], 0x1p-30, fma((double)zm[q], 0x1p-48, (double)zl[q] * 0x1p-66));
+                    out[q] = (e_r < -99999 || ef < -99999) ? 0.0 : ldexp(v, e_r + ef);
+                }
+            } else {
+                uint32_t x[8];
+                tmem_ld8(tmem + lane_base + (uint32_t)c8, x);
+#pragma unroll
+                for (int q = 0; q < 8; q++) out[q] = (double)__uint_as_float(x[q]);
+            }
+            if (row_ok) {
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int j = j0 + c8 + q;
+                    if (j < k) {
+                        C[r + (int64_t)j * ldc] = out[q];
+                        if (C32) C32[r + (int64_t)j * ldc] = (float)out[q];
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ------------------------------------------------------------- host side
+
+template <int S, int NT, bool OZAKI>
+static size_t bs_bytes(int t, int k)
+{
+    const int nchunks = (t + kKC - 1) / kKC;
+    const int ncb = (k + NT - 1) / NT;
+    return (size_t)ncb * nchunks * S * NT * kKC * 2;
+}
+
+static size_t slices_bytes(int t, int k)
+{
+    size_t a = bs_bytes<9, 48, true>(t, k);  // 10 x 48 = 480 TMEM columns
+    size_t b = bs_bytes<3, 128, false>(t, k);
+    return ((a > b ? a : b) + 255) & ~(size_t)255;
+}
+
+// workspace: the B slices, then k column exponents
+size_t tc_gemm_ws_bytes(int t, int k) { return slices_bytes(t, k) + sizeof(int) * (size_t)k + 256; }
+
+template <int S, int NT, bool OZAKI, typename WT>
+static cudaError_t launch_tc(const WT *W, int64_t ldw, int64_t rows, int t, const double *Q, int64_t ldq,
+                             int k, double *C, int64_t ldc, float *C32, uint16_t *bs, int *fexp, int *err,
+                             cudaStream_t s)
+{
+    using Cfg = TileCfg<S, NT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<S, NT, OZAKI, WT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int nchunks = (t + kKC - 1) / kKC;
+    const int ncb = (k + NT - 1) / NT;
+    dim3 pg((unsigned)((ncb * NT + 127) / 128), (unsigned)nchunks);
+    prep_b_kernel<S, NT, OZAKI><<<pg, 128, 0, s>>>(Q, ldq, t, k, nchunks, ncb, bs, fexp);
+    dim3 grid((unsigned)((rows + kTM - 1) / kTM), (unsigned)ncb);
+    tc_gemm_kernel<S, NT, OZAKI, WT><<<grid, kThreads, Cfg::smem_bytes, s>>>(W, ldw, rows, t, k, bs, fexp,
+                                                                          nchunks, C, ldc, C32, err);
+    return cudaGetLastError();
+}
+
+// mode 0: FP64 (Ozaki digits), mode 1: three BF16 pieces with FP32 accumulation.
+cudaError_t tc_gemm(int mode, const double *W, const float *W32, int64_t ldw, int64_t rows, int t,
+                    const double *Q, int64_t ldq, int k, double *C, int64_t ldc, float *C32, void *ws,
+                    int *err, cudaStream_t s, int *launches)
+{
+    if (t < 1 || k < 1 || rows < 1) return cudaErrorInvalidValue;
+    if (mode == 0 && t > kMaxT) return cudaErrorInvalidValue;
+    uint16_t *bs = (uint16_t *)ws;
+    int *fx = (int *)((uint8_t *)ws + slices_bytes(t, k));
+    if (launches) *launches += 2;
+    if (mode == 0) return launch_tc<9, 48, true, double>(W, ldw, rows, t, Q, ldq, k, C, ldc, C32, bs, fx, err, s);
+    if (W32) return launch_tc<3, 128, false, float>(W32, ldw, rows, t, Q, ldq, k, C, ldc, C32, bs, fx, err, s);
+    return launch_tc<3, 128, false, double>(W, ldw, rows, t, Q, ldq, k, C, ldc, C32, bs, fx, err, s);
+}
+
+}  // namespace svdsc

@@ -105,4 +105,10 @@ cudaError_t small_svd(int t, const double *T, int64_t ldt, double *S, double *Uh
                       SvdWork &w, DevStatus *st, cudaStream_t s, int *launches);
 int small_svd_coop_capacity();
 
+// ---- tensor-core restart GEMM (gemm_tc.cu)
+size_t tc_gemm_ws_bytes(int t, int k);
+cudaError_t tc_gemm(int mode, const double *W, const float *W32, int64_t ldw, int64_t rows, int t,
+                    const double *Q, int64_t ldq, int k, double *C, int64_t ldc, float *C32, void *ws,
+                    int *err, cudaStream_t s, int *launches);
+
 }  // namespace svdsc

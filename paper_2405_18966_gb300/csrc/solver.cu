@@ -36,6 +36,12 @@ struct svdsc_ctx {
     int64_t ldu = 0, ldv = 0;
     double *U = nullptr, *V = nullptr, *T = nullptr;
     float *U32 = nullptr, *V32 = nullptr;
+    // second bases: the tensor-core restart GEMM writes out of place and the
+    // two sets swap roles at every restart
+    double *Ua = nullptr, *Va = nullptr;
+    float *U32a = nullptr, *V32a = nullptr;
+    void *gemm_ws = nullptr;
+    int restart_gemm = 0;
     double *P = nullptr, *h = nullptr, *Pn = nullptr;
     double *Sh = nullptr, *Uh = nullptr, *Vh = nullptr, *res = nullptr, *rho = nullptr;
     SvdWork svd;
@@ -238,6 +244,23 @@ static int gemm_inplace(svdsc_ctx *c, double *W, int64_t ld, int64_t rows, int t
     return SVDSC_OK;
 }
 
+// Out-of-place tensor-core update C = W Q (svdsc_gemm modes): FP64 digits, or
+// three BF16 pieces of the FP32 shadow in the mixed form (C32 gets the shadow).
+static int gemm_tc(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, int64_t rows, int t,
+                   const double *Q, int k, double *C, float *C32)
+{
+    const int mode = (c->precision == SVDSC_MIXED) ? 1 : 0;
+    const int e0 = ph_begin(c);
+    int nl = 0;
+    cudaError_t e = tc_gemm(mode, W, W32, ld, rows, t, Q, t, k, C, ld, C32, c->gemm_ws, &c->st->timeout,
+                            c->stream, &nl);
+    const double wb = (W32 ? 4.0 : 8.0) * rows * t;
+    const double prods = mode == 0 ? 45.0 : 6.0;
+    ph_end(c, SVDSC_PH_GEMM, e0, nl, wb + 8.0 * rows * k + (C32 ? 4.0 * rows * k : 0.0),
+           2.0 * rows * (double)t * k * prods);
+    return e == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
+}
+
 // Sign rule for returned pairs: the entry of v_j with the largest magnitude
 // (lowest index on ties) is made positive, flipping u_j with it.
 __global__ void __launch_bounds__(256)
@@ -307,6 +330,10 @@ static void free_workspace(svdsc_ctx *c)
 {
     cudaFree(c->U); cudaFree(c->V); cudaFree(c->T);
     cudaFree(c->U32); cudaFree(c->V32);
+    cudaFree(c->Ua); cudaFree(c->Va); cudaFree(c->U32a); cudaFree(c->V32a); cudaFree(c->gemm_ws);
+    c->Ua = c->Va = nullptr;
+    c->U32a = c->V32a = nullptr;
+    c->gemm_ws = nullptr;
     cudaFree(c->P); cudaFree(c->h); cudaFree(c->Pn);
     cudaFree(c->Sh); cudaFree(c->Uh); cudaFree(c->Vh); cudaFree(c->res); cudaFree(c->rho);
     cudaFree(c->svd.B); cudaFree(c->svd.W); cudaFree(c->svd.sig); cudaFree(c->svd.rot);
@@ -332,10 +359,15 @@ static int reserve_ws(svdsc_ctx *c, int t)
     };
     alloc((void **)&c->U, sizeof(double) * c->ldu * cols);
     alloc((void **)&c->V, sizeof(double) * c->ldv * cols);
+    alloc((void **)&c->Ua, sizeof(double) * c->ldu * cols);
+    alloc((void **)&c->Va, sizeof(double) * c->ldv * cols);
+    alloc(&c->gemm_ws, tc_gemm_ws_bytes(t, t));
     alloc((void **)&c->T, sizeof(double) * (size_t)(t + 2) * (t + 2));
     if (c->precision == SVDSC_MIXED) {
         alloc((void **)&c->U32, sizeof(float) * c->ldu * cols);
         alloc((void **)&c->V32, sizeof(float) * c->ldv * cols);
+        alloc((void **)&c->U32a, sizeof(float) * c->ldu * cols);
+        alloc((void **)&c->V32a, sizeof(float) * c->ldv * cols);
     }
     alloc((void **)&c->P, sizeof(double) * (size_t)nbmax * cols);
     alloc((void **)&c->h, sizeof(double) * cols);
@@ -357,7 +389,9 @@ static int reserve_ws(svdsc_ctx *c, int t)
     }
     // zero the bases once so that stale columns never hold NaN
     if (cudaMemsetAsync(c->U, 0, sizeof(double) * c->ldu * cols, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->V, 0, sizeof(double) * c->ldv * cols, c->stream) != cudaSuccess)
+        cudaMemsetAsync(c->V, 0, sizeof(double) * c->ldv * cols, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->Ua, 0, sizeof(double) * c->ldu * cols, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->Va, 0, sizeof(double) * c->ldv * cols, c->stream) != cudaSuccess)
         return SVDSC_ERR_CUDA;
     c->t_cap = t;
     return SVDSC_OK;
@@ -599,6 +633,8 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
     c->precision = prec;
     c->seed = opt ? opt->seed : 0;
     c->timing = opt ? (opt->timing != 0) : false;
+    c->restart_gemm = opt ? opt->restart_gemm : 0;
+    if (c->restart_gemm != 0 && c->restart_gemm != 1) { delete c; return SVDSC_ERR_ARG; }
     c->format = A->format;
     c->m = A->m;
     c->n = A->n;
@@ -667,6 +703,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     if (ldu < c->m || ldv < c->n) return SVDSC_ERR_ARG;
     const int t = (p < 0) ? std::max(15, 3 * k) : k + p;
     if (t < k || t > c->m || t + 1 > c->n || k > kGemmGroups * kGemmMaxQ) return SVDSC_ERR_SIZE;
+    if (c->restart_gemm == 0 && t > 448) return SVDSC_ERR_SIZE;
     int rc = reserve_ws(c, t);
     if (rc) return rc;
     cudaStream_t s = c->stream;
@@ -746,15 +783,33 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         if (c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
         if (c->st_host->converged || it == maxit) break;
         // lines 8-12: augmented restart
-        rc = gemm_inplace(c, c->U, c->ldu, c->m, t, c->Uh, k);   // U~_k = U(:,1:t) Uh(:,1:k)
-        if (rc) return rc;
-        rc = gemm_inplace(c, c->V, c->ldv, c->n, t, c->Vh, k);   // V~_k = V(:,1:t) Vh(:,1:k)
-        if (rc) return rc;
-        CU(cudaMemcpyAsync(colV(c, k), colV(c, t), sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
-        if (c->precision == SVDSC_MIXED) {
-            copy_f64_to_f32(c->U, c->U32, c->ldu * k, s);
-            copy_f64_to_f32(c->V, c->V32, c->ldv * (k + 1), s);
-            ph_end(c, SVDSC_PH_OTHER, -1, 2, 12.0 * (c->ldu * k + c->ldv * (k + 1)), 0.0);
+        if (c->restart_gemm == 0) {
+            // U~_k = U(:,1:t) Uh(:,1:k), V~_k = V(:,1:t) Vh(:,1:k) into the other bases
+            rc = gemm_tc(c, c->U, c->U32, c->ldu, c->m, t, c->Uh, k, c->Ua, c->U32a);
+            if (rc) return rc;
+            rc = gemm_tc(c, c->V, c->V32, c->ldv, c->n, t, c->Vh, k, c->Va, c->V32a);
+            if (rc) return rc;
+            // v_{k+1} = v_{t+1}
+            CU(cudaMemcpyAsync(c->Va + (int64_t)k * c->ldv, colV(c, t), sizeof(double) * c->n,
+                               cudaMemcpyDeviceToDevice, s));
+            if (c->V32)
+                CU(cudaMemcpyAsync(c->V32a + (int64_t)k * c->ldv, colV32(c, t), sizeof(float) * c->n,
+                                   cudaMemcpyDeviceToDevice, s));
+            std::swap(c->U, c->Ua);
+            std::swap(c->V, c->Va);
+            std::swap(c->U32, c->U32a);
+            std::swap(c->V32, c->V32a);
+        } else {
+            rc = gemm_inplace(c, c->U, c->ldu, c->m, t, c->Uh, k);   // U~_k = U(:,1:t) Uh(:,1:k)
+            if (rc) return rc;
+            rc = gemm_inplace(c, c->V, c->ldv, c->n, t, c->Vh, k);   // V~_k = V(:,1:t) Vh(:,1:k)
+            if (rc) return rc;
+            CU(cudaMemcpyAsync(colV(c, k), colV(c, t), sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+            if (c->precision == SVDSC_MIXED) {
+                copy_f64_to_f32(c->U, c->U32, c->ldu * k, s);
+                copy_f64_to_f32(c->V, c->V32, c->ldv * (k + 1), s);
+                ph_end(c, SVDSC_PH_OTHER, -1, 2, 12.0 * (c->ldu * k + c->ldv * (k + 1)), 0.0);
+            }
         }
         restart_T_kernel<<<1, 256, 0, s>>>(t, k, c->T, c->Sh, c->rho);
         ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0);
@@ -778,22 +833,33 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     }
     const DevStatus fin = *c->st_host;
 
-    // lines 14-15: outputs (in place in the basis, then copied out)
-    rc = gemm_inplace(c, c->U, c->ldu, c->m, t, c->Uh, k);
-    if (rc) return rc;
-    rc = gemm_inplace(c, c->V, c->ldv, c->n, t, c->Vh, k);
-    if (rc) return rc;
-    sign_kernel<<<k, 256, 0, s>>>(c->U, c->ldu, c->m, c->V, c->ldv, c->n);
+    // lines 14-15: outputs (into the spare bases or in place, then copied out)
+    double *Uo = c->U, *Vo = c->V;
+    if (c->restart_gemm == 0) {
+        rc = gemm_tc(c, c->U, c->U32, c->ldu, c->m, t, c->Uh, k, c->Ua, nullptr);
+        if (rc) return rc;
+        rc = gemm_tc(c, c->V, c->V32, c->ldv, c->n, t, c->Vh, k, c->Va, nullptr);
+        if (rc) return rc;
+        Uo = c->Ua;
+        Vo = c->Va;
+    } else {
+        rc = gemm_inplace(c, c->U, c->ldu, c->m, t, c->Uh, k);
+        if (rc) return rc;
+        rc = gemm_inplace(c, c->V, c->ldv, c->n, t, c->Vh, k);
+        if (rc) return rc;
+    }
+    sign_kernel<<<k, 256, 0, s>>>(Uo, c->ldu, c->m, Vo, c->ldv, c->n);
     ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0);
     CU(cudaGetLastError());
     const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CU(cudaMemcpyAsync(S, c->Sh, sizeof(double) * k, kind, s));
     if (res) CU(cudaMemcpyAsync(res, c->res, sizeof(double) * k, kind, s));
-    CU(cudaMemcpy2DAsync(U, sizeof(double) * ldu, c->U, sizeof(double) * c->ldu, sizeof(double) * c->m, k,
+    CU(cudaMemcpy2DAsync(U, sizeof(double) * ldu, Uo, sizeof(double) * c->ldu, sizeof(double) * c->m, k,
                          kind, s));
-    CU(cudaMemcpy2DAsync(V, sizeof(double) * ldv, c->V, sizeof(double) * c->ldv, sizeof(double) * c->n, k,
+    CU(cudaMemcpy2DAsync(V, sizeof(double) * ldv, Vo, sizeof(double) * c->ldv, sizeof(double) * c->n, k,
                          kind, s));
     CU(cudaStreamSynchronize(s));
+    if (c->st_host->timeout || read_status(c) != SVDSC_OK || c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
     if (info) {
         memset(info, 0, sizeof(*info));
         info->converged = fin.converged;
@@ -849,6 +915,25 @@ int svdsc_cgs2(svdsc_ctx *c, int64_t len, int64_t ncols, const double *W, int64_
     sum_sqrt_kernel<<<1, 256, 0, c->stream>>>(c->Pn, ch->nb, norm_out);
     if (cudaGetLastError() != cudaSuccess) return SVDSC_ERR_CUDA;
     return cudaStreamSynchronize(c->stream) == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
+}
+
+int svdsc_gemm(svdsc_ctx *c, int mode, int64_t rows, int t, int k, const double *W, int64_t ldw,
+               const double *Q, int64_t ldq, double *C, int64_t ldc)
+{
+    if (!c || !W || !Q || !C || rows < 1 || t < 1 || k < 1 || k > t || ldw < rows || ldq < t || ldc < rows)
+        return SVDSC_ERR_ARG;
+    if (mode != 0 && mode != 1) return SVDSC_ERR_ARG;
+    if (t > c->t_cap || (mode == 0 && t > 448)) return SVDSC_ERR_SIZE;
+    int nl = 0;
+    DevStatus init;
+    memset(&init, 0, sizeof(init));
+    init.bd_step = INT_MAX;
+    CU(cudaMemcpyAsync(c->st, &init, sizeof(DevStatus), cudaMemcpyHostToDevice, c->stream));
+    CU(tc_gemm(mode, W, nullptr, ldw, rows, t, Q, ldq, k, C, ldc, nullptr, c->gemm_ws, &c->st->timeout,
+               c->stream, &nl));
+    int rc = read_status(c);
+    if (rc) return rc;
+    return c->st_host->timeout ? SVDSC_ERR_TIMEOUT : SVDSC_OK;
 }
 
 int svdsc_small_svd(svdsc_ctx *c, int t, const double *T, int64_t ldt, double *S, double *Uh, double *Vh)

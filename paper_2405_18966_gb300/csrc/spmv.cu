@@ -23,11 +23,17 @@ __device__ __forceinline__ AT spmv_row_group(const int64_t *__restrict__ row_ptr
     const int64_t e0 = row_ptr[r], e1 = row_ptr[r + 1];
     AT a0 = AT(0), a1 = AT(0);
     int64_t e = e0 + lg;
-    for (; e + G < e1; e += 2 * G) {
-        a0 += AT(__ldg(val + e)) * AT(__ldg(x + __ldg(col + e)));
-        a1 += AT(__ldg(val + e + G)) * AT(__ldg(x + __ldg(col + e + G)));
+    for (; e + 3 * G < e1; e += 4 * G) {  // four independent loads in flight per lane
+        const int32_t c0 = __ldg(col + e), c1 = __ldg(col + e + G), c2 = __ldg(col + e + 2 * G),
+                      c3 = __ldg(col + e + 3 * G);
+        const VT v0 = __ldg(val + e), v1 = __ldg(val + e + G), v2 = __ldg(val + e + 2 * G),
+                 v3 = __ldg(val + e + 3 * G);
+        a0 += AT(v0) * AT(__ldg(x + c0));
+        a1 += AT(v1) * AT(__ldg(x + c1));
+        a0 += AT(v2) * AT(__ldg(x + c2));
+        a1 += AT(v3) * AT(__ldg(x + c3));
     }
-    if (e < e1) a0 += AT(__ldg(val + e)) * AT(__ldg(x + __ldg(col + e)));
+    for (; e < e1; e += G) a0 += AT(__ldg(val + e)) * AT(__ldg(x + __ldg(col + e)));
     AT s = a0 + a1;
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
@@ -485,15 +491,18 @@ __global__ void transpose_fill(const int64_t *__restrict__ keys, int64_t nnz,
         if (e_ != cudaSuccess) { rc = SVDSC_ERR_CUDA; goto done; } \
     } while (0)
 
+// Lanes per row are chosen so that each lane does >= 4 FMAs: on GB300 every
+// warp-wide FP64 instruction occupies the FP64 pipe for 16 SM cycles, so a
+// shuffle reduction over many lanes of a short row costs more than its FMAs.
 static int bin_of(int64_t len)
 {
-    if (len <= 2) return 0;
-    if (len <= 4) return 1;
-    if (len <= 8) return 2;
-    if (len <= 16) return 3;
-    if (len <= 32) return 4;
-    if (len <= 4096) return 5;
-    return 6;
+    if (len <= 8) return 0;      // 1 lane per row
+    if (len <= 16) return 1;     // 2
+    if (len <= 32) return 2;     // 4
+    if (len <= 64) return 3;     // 8
+    if (len <= 128) return 4;    // 16
+    if (len <= 4096) return 5;   // 32 (a warp)
+    return 6;                    // a CTA
 }
 
 // Groups rows by bin (ascending row order inside a bin) and uploads perm.

@@ -292,3 +292,54 @@ def test_mixed_precision_k100_vs_fp64_oracle(pkg, orc):
                  1e-10, 100, precision="mixed", v0=v0)
     rel = np.abs(r.S - ref["S"]) / ref["S"]
     assert rel.max() <= 1e-6, rel.max()
+
+
+# ------------------------------------------------- tensor-core restart GEMM
+
+@pytest.mark.parametrize("rows,t,k", [(1, 1, 1), (127, 16, 10), (128, 20, 10), (1000, 33, 49),
+                                      (50_001, 200, 100), (3000, 448, 48), (4096, 64, 64)])
+def test_tc_gemm_fp64_digits_vs_oracle(pkg, orc, torch_mod, rows, t, k):
+    """Mode 0 (Ozaki-style digits on BF16 tcgen05 MMAs) against the oracle's FP64
+    loop: error within 8 eps sum_c |W_rc| |Q_cj| (an FP64 GEMM's bound) plus
+    the digit split's own bound 2^-47 max|W_r| max|Q_j|."""
+    torch = torch_mod
+    rng = np.random.default_rng(rows + t + k)
+    W = rng.standard_normal((rows, t)) / np.sqrt(rows)
+    W[0, :] *= 1e-300 if rows > 2 else 1.0        # tiny row
+    if rows > 3:
+        W[2, :] = 0.0                                # zero row
+        W[3, ::2] *= 1e-12                           # wide range inside one row
+    Q = np.linalg.qr(rng.standard_normal((t, t)))[0][:, :k]
+    ref = orc.gemm(W, Q)
+    bound = (8 * 2.0**-53 * (np.abs(W) @ np.abs(Q))
+             + 2.0**-47 * np.outer(np.abs(W).max(axis=1), np.abs(Q).max(axis=0)) + 1e-320)
+    A = synth.csr_uniform(600, 600, 0.01, 1)
+    with pkg.Solver(A) as s:
+        s.reserve(max(t, 2))
+        C = s.gemm(torch.tensor(W, device="cuda"), torch.tensor(Q, device="cuda"), mode=0).cpu().numpy()
+    err = np.abs(C - ref)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def test_tc_gemm_mixed_pieces(pkg, orc, torch_mod):
+    torch = torch_mod
+    rng = np.random.default_rng(3)
+    W = rng.standard_normal((20_000, 200)) / 140.0
+    Q = np.linalg.qr(rng.standard_normal((200, 200)))[0][:, :100]
+    ref = orc.gemm(W.astype(np.float32).astype(np.float64), Q)
+    A = synth.csr_uniform(600, 600, 0.01, 1)
+    with pkg.Solver(A) as s:
+        s.reserve(200)
+        C = s.gemm(torch.tensor(W, device="cuda"), torch.tensor(Q, device="cuda"), mode=1).cpu().numpy()
+    scale = np.abs(W) @ np.abs(Q)
+    assert np.max(np.abs(C - ref) / scale) < 2e-6
+
+
+@pytest.mark.parametrize("gemm", ["tensor", "fma"])
+def test_solve_both_restart_gemms(pkg, orc, gemm):
+    a = synth.workload_sparse_zipf(0.01)
+    v0 = synth.start_vector(a.n, 5)
+    r = pkg.svds(a, 12, 12, 1e-10, 100, v0=v0, restart_gemm=gemm)
+    ref = orc.svds(a, 12, 12, 1e-10, 100, v0=v0)
+    assert r.info["converged"] == 1
+    _compare(r, ref, 12)
