@@ -253,6 +253,48 @@ int svdsc_gemm(svdsc_ctx *ctx, int mode, int64_t rows, int t, int k, const doubl
 int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, int64_t ldw, double *w,
                        double *norm_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent truncated SVDs (uneven shapes and k) solved
+ * in ONE persistent kernel launch, replayed from a CUDA graph.  One CTA per SM
+ * takes matrices from a work queue (largest estimated cost first) and runs
+ * Alg. 2 for each from start to finish.  Precision is the mixed form (FP32
+ * CSR values, FP32 SpMV and first CGS pass, FP64 second pass, norms, projected
+ * SVD and residual test, FP32 restart GEMM); options.precision must be
+ * SVDSC_MIXED.  Limits per matrix: CSR input, 1 <= k <= 48, t = k + p <= 80
+ * (p < 0: t = max(15, 3k)), t <= m, t + 1 <= n (SVDSC_ERR_SIZE otherwise).
+ * Matrix b uses seed options.seed + b for its random start vector.
+ */
+typedef struct svdsc_batch svdsc_batch;
+
+/* Copies and prepares all nb matrices (as svdsc_create does), sizes one
+ * workspace slot per resident CTA, and runs the autotuner: for each
+ * matrix-shape class (average row length and row count of A and of A^T, basis
+ * length and size) it times the SpMV lanes-per-row candidates 1..32 and the
+ * CGS projection column tiles 1, 2, 4 on all SMs and keeps the fastest
+ * (cached for the process).  Work runs on an internal stream; `stream` is
+ * ignored (the graph needs a capturable stream). */
+int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const int *k, const int *p,
+                       const svdsc_options *opt, void *stream);
+
+/* Solves every matrix.  S[b] (k_b), U[b] (m_b x k_b, ld m_b), V[b] (n_b x k_b,
+ * ld n_b), res[b] (k_b, or res / res[b] NULL): device pointers when
+ * out_on_device, else host.  infos (nb entries, may be NULL) report per-matrix
+ * convergence, restarts and products (reserved = the matrix's error code).
+ * Returns the most severe per-matrix status. */
+int svdsc_batch_solve(svdsc_batch *b, double tol, int maxit, double *const *S, double *const *U,
+                      double *const *V, double *const *res, int out_on_device, svdsc_info *infos);
+
+/* The autotuner's choice for matrix i and the total tuning time. */
+int svdsc_batch_tuning(const svdsc_batch *b, int i, int *lanes_A, int *lanes_AT, int *gemv_cols,
+                       double *tune_ms);
+
+int svdsc_batch_destroy(svdsc_batch *b);
+
+/* One call: create, solve, destroy. */
+int svdsc_solve_batched(int nb, const svdsc_matrix *As, const int *k, const int *p, double tol, int maxit,
+                        double *const *S, double *const *U, double *const *V, double *const *res,
+                        int out_on_device, const svdsc_options *opt, svdsc_info *infos);
+
 #ifdef __cplusplus
 }
 #endif

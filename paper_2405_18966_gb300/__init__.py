@@ -32,7 +32,8 @@ F64, F32 = 0, 1
 # Every symbol include/svdsc.h declares.
 EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "svdsc_matvec",
            "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc",
-           "svdsc_gemm")
+           "svdsc_gemm", "svdsc_batch_create", "svdsc_batch_solve", "svdsc_batch_tuning",
+           "svdsc_batch_destroy", "svdsc_solve_batched")
 
 
 class SvdscMatrix(C.Structure):
@@ -92,6 +93,14 @@ def lib():
         L.svdsc_reserve.argtypes = [vp, i32]
         L.svdsc_cgs2_noalloc.argtypes = [i64, i64, vp, i64, vp, vp, vp]
         L.svdsc_gemm.argtypes = [vp, i32, i64, i32, i32, vp, i64, vp, i64, vp, i64]
+        L.svdsc_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(SvdscMatrix), vp, vp,
+                                         C.POINTER(SvdscOptions), vp]
+        L.svdsc_batch_solve.argtypes = [vp, dbl, i32, vp, vp, vp, vp, i32, C.POINTER(SvdscInfo)]
+        L.svdsc_batch_tuning.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                         C.POINTER(dbl)]
+        L.svdsc_batch_destroy.argtypes = [vp]
+        L.svdsc_solve_batched.argtypes = [i32, C.POINTER(SvdscMatrix), vp, vp, dbl, i32, vp, vp, vp, vp,
+                                          i32, C.POINTER(SvdscOptions), C.POINTER(SvdscInfo)]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or C.c_int
         L.svdsc_strerror.restype = C.c_char_p
@@ -277,6 +286,84 @@ class Solver:
         _check(lib().svdsc_small_svd(self.handle, t, _ptr(Tc), t, _ptr(S), _ptr(Uh), _ptr(Vh)),
                "svdsc_small_svd")
         return S, Uh.t(), Vh.t()
+
+
+def _csr_struct(A, keep):
+    """SvdscMatrix for a host CSR object (values kept as float32 or float64)."""
+    rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(A.values)
+    if va.dtype not in (np.float64, np.float32):
+        va = va.astype(np.float64)
+    keep += [rp, ci, va]
+    mat = SvdscMatrix()
+    mat.format, mat.index_base = CSR_FORMAT, int(getattr(A, "index_base", 0))
+    mat.m, mat.n = int(A.m), int(A.n)
+    mat.row_ptr, mat.col_idx, mat.values = _ptr(rp), _ptr(ci), _ptr(va)
+    mat.value_type = F32 if va.dtype == np.float32 else F64
+    return mat
+
+
+class Batch:
+    """Many truncated SVDs in one persistent launch (svdsc_batch_*), mixed precision."""
+
+    def __init__(self, mats, k, p=None, seed: int = 0):
+        keep = []
+        nb = len(mats)
+        arr = (SvdscMatrix * nb)(*[_csr_struct(a, keep) for a in mats])
+        self.k = np.ascontiguousarray(k, dtype=np.int32)
+        self.p = np.ascontiguousarray(p if p is not None else self.k, dtype=np.int32)
+        self.shapes = [(int(a.m), int(a.n)) for a in mats]
+        opt = SvdscOptions(MIXED, 0, seed, 0, 0)
+        self.handle = C.c_void_p()
+        _check(lib().svdsc_batch_create(C.byref(self.handle), nb, arr, _ptr(self.k), _ptr(self.p),
+                                        C.byref(opt), None), "svdsc_batch_create")
+
+    def tuning(self, i):
+        a, b, c, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        _check(lib().svdsc_batch_tuning(self.handle, i, C.byref(a), C.byref(b), C.byref(c), C.byref(ms)),
+               "svdsc_batch_tuning")
+        return {"lanes_A": a.value, "lanes_AT": b.value, "gemv_cols": c.value, "tune_ms": ms.value}
+
+    def solve(self, tol: float = 1e-10, maxit: int = 100, out: str = "host"):
+        nb = len(self.shapes)
+        infos = (SvdscInfo * nb)()
+        if out == "host":
+            S = [np.zeros(int(k)) for k in self.k]
+            R = [np.zeros(int(k)) for k in self.k]
+            U = [np.zeros((m, int(k)), order="F") for (m, n), k in zip(self.shapes, self.k)]
+            V = [np.zeros((n, int(k)), order="F") for (m, n), k in zip(self.shapes, self.k)]
+            on_dev = 0
+        else:
+            import torch
+            S = [torch.zeros(int(k), dtype=torch.float64, device="cuda") for k in self.k]
+            R = [torch.zeros(int(k), dtype=torch.float64, device="cuda") for k in self.k]
+            U = [torch.zeros((int(k), m), dtype=torch.float64, device="cuda") for (m, n), k in zip(self.shapes, self.k)]
+            V = [torch.zeros((int(k), n), dtype=torch.float64, device="cuda") for (m, n), k in zip(self.shapes, self.k)]
+            on_dev = 1
+        ptrs = lambda xs: (C.c_void_p * nb)(*[_ptr(x).value for x in xs])
+        status = _check(lib().svdsc_batch_solve(self.handle, tol, maxit, ptrs(S), ptrs(U), ptrs(V), ptrs(R),
+                                                on_dev, infos), "svdsc_batch_solve")
+        if on_dev:
+            U = [u.t() for u in U]
+            V = [v.t() for v in V]
+        infl = []
+        for i in range(nb):
+            d = infos[i].as_dict()
+            d["err"] = infos[i].reserved
+            infl.append(d)
+        return {"S": S, "U": U, "V": V, "res": R, "infos": infl, "status": status}
+
+    def close(self):
+        if self.handle:
+            lib().svdsc_batch_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, precision: str = "fp64",

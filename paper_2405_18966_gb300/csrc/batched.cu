@@ -1,0 +1,984 @@
+// Batched form: many independent truncated SVDs (uneven shapes and k) in ONE
+// persistent launch.  One CTA per SM takes matrices from an atomic work queue
+// (largest estimated cost first) and runs Alg. 2 of the svds-C paper for each
+// from start to finish: Lanczos bidiagonalization with CGS2 full
+// re-orthogonalization, the projected SVD (one-sided Jacobi in shared memory),
+// the Eq. (4) residual test and the augmented restart, then the outputs.
+// Precision is the mixed form: FP32 CSR values, FP32 SpMV with FP32
+// accumulation, FP32 first CGS pass on FP32 basis shadows, FP64 second pass,
+// norms, projected SVD and residuals, FP32 restart GEMM.  A CTA synchronizes
+// only with itself, so nothing waits across CTAs.  The launch (with the
+// parameter upload and queue reset) is captured once in a CUDA graph and
+// replayed by every solve.  SpMV lanes-per-row and the GEMV-T column tile are
+// chosen per matrix-shape class by timing the candidates (autotuner below).
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+#include "internal.cuh"
+
+namespace svdsc {
+
+constexpr int kBT = 512;          // threads per CTA
+constexpr int kBW = kBT / 32;     // warps per CTA
+constexpr int kBMaxT = 80;        // subspace limit of the batched form (shared-memory Jacobi)
+constexpr int kBMaxK = 48;        // rank limit (register accumulators of the GEMM)
+
+struct BMat {
+    int64_t m, n, nnz;
+    int k, t;
+    const int64_t *rp, *rpT;
+    const int32_t *col, *colT;
+    const float *val, *valT;
+    double *S, *U, *V, *res;   // outputs (device), U: m x k (ld m), V: n x k (ld n)
+    int gA, gAT, tc, pad;      // tuned: lanes per row for A and A^T, GEMV-T columns per warp
+    uint64_t seed;
+};
+
+struct BStat {
+    int converged, nconv, restarts, breakdowns;
+    int64_t n_matvec, n_steps;
+    double anorm, beta_t;
+    int err, svd_sweeps;
+};
+
+struct BSlot {
+    double *U0, *U1, *V0, *V1, *T;
+    float *U32_0, *U32_1, *V32_0, *V32_1;
+    int64_t ldu, ldv;
+};
+
+struct BParams {
+    double tol;
+    int maxit, nb;
+};
+
+// shared-memory layout (doubles)
+constexpr int kSmB = 0;                               // B: t x t (Jacobi columns)
+constexpr int kSmW = kSmB + kBMaxT * kBMaxT;          // W: t x t (rotations)
+constexpr int kSmS = kSmW + kBMaxT * kBMaxT;          // sorted sigma (t)
+constexpr int kSmUt = kSmS + kBMaxT;                  // Uh(t, j) for j < k
+constexpr int kSmRho = kSmUt + kBMaxT;                // rho (k)
+constexpr int kSmH = kSmRho + kBMaxT;                 // projection coefficients (t + 2)
+constexpr int kSmRed = kSmH + kBMaxT + 8;             // reductions (4 x warps)
+constexpr int kSmSig = kSmRed + 4 * kBW;              // unsorted sigma (t)
+constexpr int kSmDoubles = kSmSig + kBMaxT;
+// floats after the doubles: Q_U (t x k), Q_V (t x k), h32 (t + 2)
+constexpr int kSmQU = 0;
+constexpr int kSmQV = kSmQU + kBMaxT * kBMaxK;
+constexpr int kSmH32 = kSmQV + kBMaxT * kBMaxK;
+constexpr int kSmFloats = kSmH32 + kBMaxT + 8;
+constexpr size_t kSmBytes = sizeof(double) * kSmDoubles + sizeof(float) * kSmFloats + 64;
+
+// ------------------------------------------------------------ CTA helpers
+
+// Deterministic CTA sum: every thread adds the warp partials in the same order.
+__device__ __forceinline__ double cta_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kBW; w++) t += red[w];
+    return t;
+}
+
+template <int G>
+__device__ void cta_spmv_g(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           const float *__restrict__ val, const float *__restrict__ x, int64_t rows,
+                           const double *__restrict__ z, double coef, double *__restrict__ y)
+{
+    const int grp = threadIdx.x / G, lg = threadIdx.x % G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+    for (int64_t r = grp; r < rows; r += kBT / G) {
+        const int64_t e0 = rp[r], e1 = rp[r + 1];
+        float a0 = 0.f, a1 = 0.f;
+        int64_t e = e0 + lg;
+        for (; e + G < e1; e += 2 * G) {
+            a0 = fmaf(__ldg(val + e), __ldg(x + __ldg(col + e)), a0);
+            a1 = fmaf(__ldg(val + e + G), __ldg(x + __ldg(col + e + G)), a1);
+        }
+        if (e < e1) a0 = fmaf(__ldg(val + e), __ldg(x + __ldg(col + e)), a0);
+        float s = a0 + a1;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
+        if (lg == 0) y[r] = (double)s - (z ? coef * z[r] : 0.0);
+    }
+}
+
+// y = A x - coef z with FP32 values, FP32 x and FP32 accumulation
+__device__ void cta_spmv(int G, const int64_t *rp, const int32_t *col, const float *val, const float *x,
+                         int64_t rows, const double *z, double coef, double *y)
+{
+    switch (G) {
+    case 1: cta_spmv_g<1>(rp, col, val, x, rows, z, coef, y); break;
+    case 2: cta_spmv_g<2>(rp, col, val, x, rows, z, coef, y); break;
+    case 4: cta_spmv_g<4>(rp, col, val, x, rows, z, coef, y); break;
+    case 8: cta_spmv_g<8>(rp, col, val, x, rows, z, coef, y); break;
+    case 16: cta_spmv_g<16>(rp, col, val, x, rows, z, coef, y); break;
+    default: cta_spmv_g<32>(rp, col, val, x, rows, z, coef, y); break;
+    }
+    __syncthreads();
+}
+
+// h[c] = W(:, c)^T w for c < ncols; a warp owns TC columns at a time and each
+// lane keeps 4 rows x (TC + 1) independent loads in flight (one SM works on
+// the whole matrix, so memory-level parallelism sets its bandwidth).
+template <typename WT, int TC>
+__device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, const double *__restrict__ w,
+                           int64_t len, double *h)
+{
+    using AT = WT;  // FP32 products and sums for the FP32 shadow, FP64 otherwise
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c0 = warp * TC; c0 < ncols; c0 += kBW * TC) {
+        AT acc[TC];
+#pragma unroll
+        for (int q = 0; q < TC; q++) acc[q] = AT(0);
+        const WT *col[TC];
+#pragma unroll
+        for (int q = 0; q < TC; q++) col[q] = W + (int64_t)min(c0 + q, ncols - 1) * ld;
+        int64_t r = lane;
+        for (; r + 96 < len; r += 128) {
+            AT wr[4];
+            WT v[TC][4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) wr[u] = (AT)__ldg(w + r + 32 * u);
+#pragma unroll
+            for (int q = 0; q < TC; q++)
+#pragma unroll
+                for (int u = 0; u < 4; u++) v[q][u] = __ldcs(col[q] + r + 32 * u);
+#pragma unroll
+            for (int q = 0; q < TC; q++)
+#pragma unroll
+                for (int u = 0; u < 4; u++) acc[q] = fma((AT)v[q][u], wr[u], acc[q]);
+        }
+        for (; r < len; r += 32) {
+            const AT wr = (AT)w[r];
+#pragma unroll
+            for (int q = 0; q < TC; q++) acc[q] = fma((AT)col[q][r], wr, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < TC; q++) {
+            double s = (double)acc[q];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0 && c0 + q < ncols) h[c0 + q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename WT>
+__device__ void cta_proj(int tc, const WT *W, int64_t ld, int ncols, const double *w, int64_t len, double *h)
+{
+    if (tc >= 4) cta_proj_t<WT, 4>(W, ld, ncols, w, len, h);
+    else if (tc == 2) cta_proj_t<WT, 2>(W, ld, ncols, w, len, h);
+    else cta_proj_t<WT, 1>(W, ld, ncols, w, len, h);
+}
+
+// w -= W h; returns sum of the new w^2 (CTA-wide, deterministic) if asked.
+// Each thread owns two adjacent rows and keeps 8 column loads in flight.
+template <typename WT, typename HT>
+__device__ double cta_update(const WT *__restrict__ W, int64_t ld, int ncols, const HT *__restrict__ h,
+                             double *__restrict__ w, int64_t len, bool want_norm, double *red)
+{
+    double nrm = 0.0;
+    for (int64_t r = 2 * threadIdx.x; r < len; r += 2 * kBT) {
+        const bool two = r + 1 < len;
+        WT a0 = WT(0), a1 = WT(0), b0 = WT(0), b1 = WT(0);
+        int c = 0;
+        if (two) {
+            for (; c + 3 < ncols; c += 4) {
+                WT x[4], y[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    x[u] = __ldcs(W + r + (int64_t)(c + u) * ld);
+                    y[u] = __ldcs(W + r + 1 + (int64_t)(c + u) * ld);
+                }
+                a0 = fma(x[0], (WT)h[c], a0); a1 = fma(y[0], (WT)h[c], a1);
+                b0 = fma(x[1], (WT)h[c + 1], b0); b1 = fma(y[1], (WT)h[c + 1], b1);
+                a0 = fma(x[2], (WT)h[c + 2], a0); a1 = fma(y[2], (WT)h[c + 2], a1);
+                b0 = fma(x[3], (WT)h[c + 3], b0); b1 = fma(y[3], (WT)h[c + 3], b1);
+            }
+            for (; c < ncols; c++) {
+                a0 = fma(W[r + (int64_t)c * ld], (WT)h[c], a0);
+                a1 = fma(W[r + 1 + (int64_t)c * ld], (WT)h[c], a1);
+            }
+            const double n0 = w[r] - (double)(a0 + b0);
+            const double n1 = w[r + 1] - (double)(a1 + b1);
+            w[r] = n0;
+            w[r + 1] = n1;
+            nrm = fma(n0, n0, nrm);
+            nrm = fma(n1, n1, nrm);
+        } else {
+            for (; c < ncols; c++) a0 = fma(W[r + (int64_t)c * ld], (WT)h[c], a0);
+            const double n0 = w[r] - (double)a0;
+            w[r] = n0;
+            nrm = fma(n0, n0, nrm);
+        }
+    }
+    __syncthreads();
+    return want_norm ? cta_sum(nrm, red) : 0.0;
+}
+
+__device__ double cta_norm2(const double *w, int64_t len, double *red)
+{
+    double nrm = 0.0;
+    for (int64_t r = threadIdx.x; r < len; r += kBT) nrm = fma(w[r], w[r], nrm);
+    return cta_sum(nrm, red);
+}
+
+// CGS2 against ncols columns: pass 1 on the FP32 shadow, pass 2 in FP64.
+// Returns ||w||^2 after the second pass.
+__device__ double cta_cgs2(int tc, const double *W, const float *W32, int64_t ld, int ncols, double *w,
+                           int64_t len, double *h, float *h32, double *red)
+{
+    if (ncols <= 0) return cta_norm2(w, len, red);
+    cta_proj<float>(tc, W32, ld, ncols, w, len, h);
+    for (int c = threadIdx.x; c < ncols; c += kBT) h32[c] = (float)h[c];
+    __syncthreads();
+    cta_update<float, float>(W32, ld, ncols, h32, w, len, false, red);
+    cta_proj<double>(tc, W, ld, ncols, w, len, h);
+    return cta_update<double, double>(W, ld, ncols, h, w, len, true, red);
+}
+
+__device__ void cta_scale(double *w, float *w32, int64_t len, double inv)
+{
+    for (int64_t r = threadIdx.x; r < len; r += kBT) {
+        const double x = w[r] * inv;
+        w[r] = x;
+        w32[r] = (float)x;
+    }
+    __syncthreads();
+}
+
+struct BRun {
+    const BMat *M;
+    BStat *st;
+    double *U, *V, *Ua, *Va, *T;
+    float *U32, *V32, *U32a, *V32a;
+    int64_t ldu, ldv, m, n;
+    int t, k, tc;
+    uint64_t key, draws;
+    double anorm;
+    double *sm;
+    float *smf;
+    bool failed;
+};
+
+__device__ __forceinline__ double *Tb(BRun &R, int r, int c) { return R.T + r + (int64_t)c * (R.t + 1); }
+
+// Normalises the freshly orthogonalized column `col` of side (0: U, 1: V);
+// a breakdown (norm <= 1e-13 * largest alpha/beta/sigma so far) draws random
+// replacement vectors.  Returns the T entry (0 after a breakdown).
+__device__ double finish_vector(BRun &R, int side, int col, double nrm2)
+{
+    const int64_t len = side ? R.n : R.m;
+    double *W = side ? R.V : R.U;
+    float *W32 = side ? R.V32 : R.U32;
+    const int64_t ld = side ? R.ldv : R.ldu;
+    double *w = W + (int64_t)col * ld;
+    float *w32 = W32 + (int64_t)col * ld;
+    double *red = R.sm + kSmRed;
+    const double nrm = sqrt(nrm2);
+    if (!isfinite(nrm)) {
+        R.failed = true;
+        if (threadIdx.x == 0) R.st->err = SVDSC_ERR_NONFINITE;
+        return 0.0;
+    }
+    if (nrm > 1e-13 * R.anorm) {
+        if (nrm > R.anorm) R.anorm = nrm;
+        cta_scale(w, w32, len, 1.0 / nrm);
+        return nrm;
+    }
+    if (threadIdx.x == 0) R.st->breakdowns++;
+    for (int attempt = 0; attempt < 8; attempt++) {
+        const uint64_t d = R.draws++;
+        for (int64_t j = threadIdx.x; j < len; j += kBT) w[j] = normal_draw(R.key, d, (uint64_t)j);
+        __syncthreads();
+        const double n2 = cta_cgs2(R.tc, W, W32, ld, col, w, len, R.sm + kSmH, R.smf + kSmH32, red);
+        const double nr = sqrt(n2);
+        if (nr > 1e-8 && isfinite(nr)) {
+            cta_scale(w, w32, len, 1.0 / nr);
+            return 0.0;
+        }
+    }
+    for (int64_t j = threadIdx.x; j < len; j += kBT) { w[j] = 0.0; w32[j] = 0.f; }
+    __syncthreads();
+    return 0.0;
+}
+
+// Alg. 1 for iterations i = s..t (u_{t+1} not formed)
+__device__ void lbp_from(BRun &R, int s)
+{
+    const BMat &M = *R.M;
+    double *red = R.sm + kSmRed;
+    for (int i = s; i <= R.t && !R.failed; i++) {
+        // v_{i+1} = A^T u_i - alpha_i v_i, CGS2 against v_1..v_i
+        double *vout = R.V + (int64_t)i * R.ldv;
+        cta_spmv(M.gAT, M.rpT, M.colT, M.valT, R.U32 + (int64_t)(i - 1) * R.ldu, R.n,
+                 R.V + (int64_t)(i - 1) * R.ldv, *Tb(R, i - 1, i - 1), vout);
+        double n2 = cta_cgs2(R.tc, R.V, R.V32, R.ldv, i, vout, R.n, R.sm + kSmH, R.smf + kSmH32, red);
+        const double beta = finish_vector(R, 1, i, n2);
+        if (threadIdx.x == 0) *Tb(R, i - 1, i) = beta;
+        __syncthreads();
+        if (threadIdx.x == 0) { R.st->n_matvec++; R.st->n_steps++; }
+        if (i == R.t) break;
+        // u_{i+1} = A v_{i+1} - beta_i u_i, CGS2 against u_1..u_i
+        double *uout = R.U + (int64_t)i * R.ldu;
+        cta_spmv(M.gA, M.rp, M.col, M.val, R.V32 + (int64_t)i * R.ldv, R.m, R.U + (int64_t)(i - 1) * R.ldu,
+                 beta, uout);
+        n2 = cta_cgs2(R.tc, R.U, R.U32, R.ldu, i, uout, R.m, R.sm + kSmH, R.smf + kSmH32, red);
+        const double alpha = finish_vector(R, 0, i, n2);
+        if (threadIdx.x == 0) *Tb(R, i, i) = alpha;
+        __syncthreads();
+        if (threadIdx.x == 0) { R.st->n_matvec++; R.st->n_steps++; }
+    }
+}
+
+// Projected SVD of T(1:t,1:t) by one-sided Jacobi in shared memory (FP64,
+// round-robin pairs, one warp per pair).  Leaves the descending sigma in
+// sm[kSmS], Uh(t, j) in sm[kSmUt] and the leading k columns of Uh and Vh (as
+// FP32) in the Q buffers.
+__device__ void cta_small_svd(BRun &R)
+{
+    const int t = R.t, k = R.k;
+    double *B = R.sm + kSmB, *Wm = R.sm + kSmW, *sig = R.sm + kSmSig, *S = R.sm + kSmS, *ut = R.sm + kSmUt;
+    float *QU = R.smf + kSmQU, *QV = R.smf + kSmQV;
+    __shared__ int rot_count;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < t * t; i += kBT) {
+        const int r = i % t, c = i / t;
+        B[r + c * t] = *Tb(R, r, c);
+        Wm[r + c * t] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const double tol = DBL_EPSILON * sqrt((double)t);
+    const int n2 = t + (t & 1);
+    int sweeps = 0;
+    bool conv = false;
+    while (sweeps < 100) {
+        if (threadIdx.x == 0) rot_count = 0;
+        __syncthreads();
+        sweeps++;
+        for (int round = 0; round < n2 - 1; round++) {
+            for (int slot = warp; slot < n2 / 2; slot += kBW) {
+                auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (n2 - 1)) + 1; };
+                int p = player(slot), q = player(n2 - 1 - slot);
+                if (p > q) { const int x = p; p = q; q = x; }
+                if (q >= t) continue;
+                double *bp = B + p * t, *bq = B + q * t;
+                double a = 0.0, b = 0.0, g = 0.0;
+                for (int r = lane; r < t; r += 32) {
+                    a += bp[r] * bp[r];
+                    b += bq[r] * bq[r];
+                    g += bp[r] * bq[r];
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    g += __shfl_xor_sync(0xffffffffu, g, o);
+                }
+                if (g == 0.0 || fabs(g) <= tol * sqrt(a * b)) continue;
+                const double zeta = (b - a) / (2.0 * g);
+                const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+                if (lane == 0) atomicAdd(&rot_count, 1);
+                for (int r = lane; r < t; r += 32) {
+                    const double x = bp[r], y = bq[r];
+                    bp[r] = c * x - s * y;
+                    bq[r] = s * x + c * y;
+                }
+                double *wp = Wm + p * t, *wq = Wm + q * t;
+                for (int r = lane; r < t; r += 32) {
+                    const double x = wp[r], y = wq[r];
+                    wp[r] = c * x - s * y;
+                    wq[r] = s * x + c * y;
+                }
+            }
+            __syncthreads();
+        }
+        if (rot_count == 0) { conv = true; break; }
+        __syncthreads();
+    }
+    for (int j = warp; j < t; j += kBW) {
+        double a = 0.0;
+        for (int r = lane; r < t; r += 32) a += B[r + j * t] * B[r + j * t];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) sig[j] = sqrt(a);
+    }
+    __syncthreads();
+    for (int j = warp; j < t; j += kBW) {
+        const double sj = sig[j];
+        int rank = 0;
+        for (int i = 0; i < t; i++) rank += (sig[i] > sj) || (sig[i] == sj && i < j);
+        if (lane == 0) {
+            S[rank] = sj;
+            if (rank < k) ut[rank] = sj > 0.0 ? B[(t - 1) + j * t] / sj : 0.0;
+        }
+        if (rank < k)
+            for (int r = lane; r < t; r += 32) {
+                QU[r + rank * t] = sj > 0.0 ? (float)(B[r + j * t] / sj) : 0.f;
+                QV[r + rank * t] = (float)Wm[r + j * t];
+            }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) R.st->svd_sweeps = conv ? sweeps : -1;
+}
+
+// C (rows x k) = W32 (rows x t) Q (t x k, FP32 in shared memory), FP32 FMA;
+// C in FP64 (and its FP32 shadow when C32 != null).
+__device__ void cta_gemm32(const float *__restrict__ W32, int64_t ld, int64_t rows, int t, const float *Q, int k,
+                           double *__restrict__ C, float *__restrict__ C32, int64_t ldc)
+{
+    for (int64_t r = threadIdx.x; r < rows; r += kBT) {
+        float acc[kBMaxK];
+#pragma unroll
+        for (int j = 0; j < kBMaxK; j++) acc[j] = 0.f;
+        for (int c = 0; c < t; c++) {
+            const float a = W32[r + (int64_t)c * ld];
+#pragma unroll
+            for (int j = 0; j < kBMaxK; j++)
+                if (j < k) acc[j] = fmaf(a, Q[c + j * t], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < kBMaxK; j++)
+            if (j < k) {
+                C[r + (int64_t)j * ldc] = (double)acc[j];
+                if (C32) C32[r + (int64_t)j * ldc] = acc[j];
+            }
+    }
+    __syncthreads();
+}
+
+// sign rule: v_j's largest-magnitude entry (lowest index on ties) positive
+__device__ void cta_sign(double *U, int64_t m, double *V, int64_t n, int k, double *red)
+{
+    __shared__ double sb[kBW];
+    __shared__ int64_t si[kBW];
+    for (int j = 0; j < k; j++) {
+        double *v = V + (int64_t)j * n;
+        double best = -1.0;
+        int64_t bi = 0;
+        for (int64_t r = threadIdx.x; r < n; r += kBT) {
+            const double a = fabs(v[r]);
+            if (a > best) { best = a; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double b2 = __shfl_xor_sync(0xffffffffu, best, o);
+            const int64_t i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (b2 > best || (b2 == best && i2 < bi)) { best = b2; bi = i2; }
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) { sb[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = bi; }
+        __syncthreads();
+        double bb = sb[0];
+        int64_t ii = si[0];
+        for (int w = 1; w < kBW; w++)
+            if (sb[w] > bb || (sb[w] == bb && si[w] < ii)) { bb = sb[w]; ii = si[w]; }
+        const bool flip = v[ii] < 0.0;
+        __syncthreads();
+        if (flip) {
+            for (int64_t r = threadIdx.x; r < n; r += kBT) v[r] = -v[r];
+            double *u = U + (int64_t)j * m;
+            for (int64_t r = threadIdx.x; r < m; r += kBT) u[r] = -u[r];
+        }
+        __syncthreads();
+    }
+    (void)red;
+}
+
+__device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, const BParams &P, double *sm, float *smf)
+{
+    BRun R;
+    R.M = &M;
+    R.st = st;
+    R.U = slot.U0; R.Ua = slot.U1; R.V = slot.V0; R.Va = slot.V1; R.T = slot.T;
+    R.U32 = slot.U32_0; R.U32a = slot.U32_1; R.V32 = slot.V32_0; R.V32a = slot.V32_1;
+    R.ldu = slot.ldu; R.ldv = slot.ldv; R.m = M.m; R.n = M.n; R.t = M.t; R.k = M.k; R.tc = M.tc;
+    R.key = splitmix_mix(M.seed);
+    R.draws = 0;
+    R.anorm = 0.0;
+    R.sm = sm;
+    R.smf = smf;
+    R.failed = false;
+    double *red = sm + kSmRed;
+    const int t = R.t, k = R.k;
+    if (threadIdx.x == 0) {
+        st->converged = 0; st->nconv = 0; st->restarts = 0; st->breakdowns = 0;
+        st->n_matvec = 0; st->n_steps = 0; st->err = 0; st->svd_sweeps = 0;
+    }
+    for (int64_t i = threadIdx.x; i < (int64_t)(t + 1) * (t + 1); i += kBT) R.T[i] = 0.0;
+    // v_1: draw 0, normalised
+    for (int64_t j = threadIdx.x; j < R.n; j += kBT) R.V[j] = normal_draw(R.key, 0, (uint64_t)j);
+    R.draws = 1;
+    __syncthreads();
+    {
+        const double nv = sqrt(cta_norm2(R.V, R.n, red));
+        cta_scale(R.V, R.V32, R.n, 1.0 / nv);
+    }
+    // u_1 = A v_1, alpha_1
+    cta_spmv(M.gA, M.rp, M.col, M.val, R.V32, R.m, nullptr, 0.0, R.U);
+    {
+        const double a1 = finish_vector(R, 0, 0, cta_norm2(R.U, R.m, red));
+        if (threadIdx.x == 0) { *Tb(R, 0, 0) = a1; st->n_matvec++; st->n_steps++; }
+        __syncthreads();
+    }
+    lbp_from(R, 1);
+    int restarts = 0;
+    for (int it = 1; it <= P.maxit && !R.failed; it++) {
+        cta_small_svd(R);
+        const double *S = sm + kSmS, *ut = sm + kSmUt;
+        double *rho = sm + kSmRho;
+        const double beta_t = *Tb(R, t - 1, t);
+        if (S[0] > R.anorm) R.anorm = S[0];
+        int nconv = 0;
+        for (int j = 0; j < k; j++) {
+            const double den = S[j] > DBL_EPSILON * S[0] ? S[j] : DBL_EPSILON * S[0];
+            const double r = den > 0.0 ? fabs(beta_t * ut[j]) / den : 0.0;
+            nconv += (r < P.tol);
+        }
+        if (threadIdx.x < k) {
+            const int j = threadIdx.x;
+            const double den = S[j] > DBL_EPSILON * S[0] ? S[j] : DBL_EPSILON * S[0];
+            M.res[j] = den > 0.0 ? fabs(beta_t * ut[j]) / den : 0.0;
+            rho[j] = beta_t * ut[j];
+        }
+        if (threadIdx.x == 0) { st->nconv = nconv; st->converged = (nconv == k); st->beta_t = beta_t; }
+        __syncthreads();
+        if (nconv == k || it == P.maxit) break;
+        // augmented restart: U~ = U(:,1:t) Uh(:,1:k), V~ = V(:,1:t) Vh(:,1:k) into the spare bases
+        cta_gemm32(R.U32, R.ldu, R.m, t, R.smf + kSmQU, k, R.Ua, R.U32a, R.ldu);
+        cta_gemm32(R.V32, R.ldv, R.n, t, R.smf + kSmQV, k, R.Va, R.V32a, R.ldv);
+        for (int64_t j = threadIdx.x; j < R.n; j += kBT) {  // v_{k+1} = v_{t+1}
+            R.Va[j + (int64_t)k * R.ldv] = R.V[j + (int64_t)t * R.ldv];
+            R.V32a[j + (int64_t)k * R.ldv] = R.V32[j + (int64_t)t * R.ldv];
+        }
+        {
+            double *x = R.U; R.U = R.Ua; R.Ua = x;
+            x = R.V; R.V = R.Va; R.Va = x;
+            float *y = R.U32; R.U32 = R.U32a; R.U32a = y;
+            y = R.V32; R.V32 = R.V32a; R.V32a = y;
+        }
+        for (int64_t i = threadIdx.x; i < (int64_t)(t + 1) * (t + 1); i += kBT) R.T[i] = 0.0;
+        __syncthreads();
+        if (threadIdx.x < k) {
+            const int j = threadIdx.x;
+            *Tb(R, j, j) = S[j];
+            *Tb(R, j, k) = rho[j];
+        }
+        __syncthreads();
+        // u_{k+1} = A v_{k+1} - U~ rho (Eq. 7), CGS2 against U~
+        double *uk = R.U + (int64_t)k * R.ldu;
+        cta_spmv(M.gA, M.rp, M.col, M.val, R.V32 + (int64_t)k * R.ldv, R.m, nullptr, 0.0, uk);
+        cta_update<double, double>(R.U, R.ldu, k, rho, uk, R.m, false, red);
+        const double n2 = cta_cgs2(R.tc, R.U, R.U32, R.ldu, k, uk, R.m, sm + kSmH, smf + kSmH32, red);
+        const double ak = finish_vector(R, 0, k, n2);
+        if (threadIdx.x == 0) { *Tb(R, k, k) = ak; st->n_matvec++; st->n_steps++; }
+        __syncthreads();
+        restarts++;
+        if (threadIdx.x == 0) st->restarts = restarts;
+        lbp_from(R, k + 1);
+    }
+    if (R.failed) return;
+    // outputs: S, U = U(:,1:t) Uh(:,1:k), V = V(:,1:t) Vh(:,1:k), sign rule
+    for (int j = threadIdx.x; j < k; j += kBT) M.S[j] = sm[kSmS + j];
+    cta_gemm32(R.U32, R.ldu, R.m, t, smf + kSmQU, k, M.U, nullptr, R.m);
+    cta_gemm32(R.V32, R.ldv, R.n, t, smf + kSmQV, k, M.V, nullptr, R.n);
+    cta_sign(M.U, R.m, M.V, R.n, k, red);
+    if (threadIdx.x == 0) st->anorm = R.anorm;
+}
+
+__global__ void __launch_bounds__(kBT, 1)
+batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, BStat *stats,
+               const BSlot *__restrict__ slots, const BParams *prm, int *queue)
+{
+    extern __shared__ __align__(16) double bsm[];
+    double *sm = bsm;
+    float *smf = (float *)(bsm + kSmDoubles);
+    __shared__ int item;
+    const BSlot slot = slots[blockIdx.x];
+    const BParams P = *prm;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int it = item;
+        if (it >= P.nb) break;
+        const int b = order[it];
+        solve_one(mats[b], stats + b, slot, P, sm, smf);
+    }
+}
+
+// ------------------------------------------------------------ autotuner
+// Times each candidate on one CTA per SM, all running the same product of the
+// class representative (the per-SM throughput the persistent kernel sees).
+__global__ void __launch_bounds__(kBT, 1)
+tune_spmv_kernel(const int64_t *rp, const int32_t *col, const float *val, const float *x, int64_t rows,
+                 double *y_slots, int64_t ldy, int G, int reps)
+{
+    double *y = y_slots + (int64_t)blockIdx.x * ldy;
+    for (int r = 0; r < reps; r++) cta_spmv(G, rp, col, val, x, rows, nullptr, 0.0, y);
+}
+
+__global__ void __launch_bounds__(kBT, 1)
+tune_proj_kernel(const double *W_slots, int64_t ldw_slot, int64_t ld, int ncols, const double *w, int64_t len,
+                 int tc, int reps)
+{
+    extern __shared__ __align__(16) double bsm[];
+    const double *W = W_slots + (int64_t)blockIdx.x * ldw_slot;
+    for (int r = 0; r < reps; r++) cta_proj<double>(tc, W, ld, ncols, w, len, bsm);
+}
+
+}  // namespace svdsc
+
+// ============================================================ host side
+using namespace svdsc;
+
+struct svdsc_batch {
+    int nb = 0;
+    int nslots = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<DevCSR> A, AT;
+    std::vector<BMat> hm;        // host copy of the descriptors
+    BMat *h_mats = nullptr;      // pinned staging copy (graph memcpy source)
+    BParams *h_prm = nullptr;    // pinned
+    BMat *d_mats = nullptr;
+    int *d_order = nullptr;
+    BStat *d_stats = nullptr;
+    BSlot *d_slots = nullptr;
+    BParams *d_prm = nullptr;
+    int *d_queue = nullptr;
+    void *slot_mem = nullptr;
+    double *out_mem = nullptr;   // device outputs when the caller wants host outputs
+    std::vector<size_t> out_off;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double tune_ms = 0.0;
+};
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune_spmv;    // (avg-len bucket, rows bucket, which) -> G
+std::map<std::tuple<int, int>, int> g_tune_proj;         // (len bucket, ncols bucket) -> columns per warp
+
+int bucket(double x) { return (int)std::lround(2.0 * std::log2(std::max(x, 1.0))); }
+
+double time_ms(cudaStream_t s, const std::function<void()> &f)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    f();  // warm
+    cudaEventRecord(a, s);
+    f();
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+}  // namespace
+
+static int tune_matrix(svdsc_batch *B, int b, int nsm, double *yscratch, int64_t ldy, float *x32, double *wsc)
+{
+    BMat &M = B->hm[b];
+    const int cand[] = {1, 2, 4, 8, 16, 32};
+    for (int which = 0; which < 2; which++) {
+        const DevCSR &C = which ? B->AT[b] : B->A[b];
+        const double avg = C.m > 0 ? (double)C.nnz / (double)C.m : 1.0;
+        const auto key = std::make_tuple(bucket(avg), bucket((double)C.m), which);
+        int best = -1;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto f = g_tune_spmv.find(key);
+            if (f != g_tune_spmv.end()) best = f->second;
+        }
+        if (best < 0) {
+            double bt = 1e30;
+            for (int G : cand) {
+                const double ms = time_ms(B->stream, [&] {
+                    tune_spmv_kernel<<<nsm, kBT, 0, B->stream>>>(C.row_ptr, C.col, C.val32, x32, C.m, yscratch, ldy,
+                                                                 G, 2);
+                });
+                B->tune_ms += 2 * ms;
+                if (ms < bt) { bt = ms; best = G; }
+            }
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_spmv[key] = best;
+        }
+        if (which) M.gAT = best; else M.gA = best;
+    }
+    {
+        const int ncols = std::max(1, M.t / 2);
+        const auto key = std::make_tuple(bucket((double)M.m), bucket((double)ncols));
+        int best = -1;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto f = g_tune_proj.find(key);
+            if (f != g_tune_proj.end()) best = f->second;
+        }
+        if (best < 0) {
+            double bt = 1e30;
+            for (int tc : {1, 2, 4}) {
+                const double ms = time_ms(B->stream, [&] {
+                    tune_proj_kernel<<<nsm, kBT, sizeof(double) * (kBMaxT + 8), B->stream>>>(
+                        wsc, 0, M.m, ncols, wsc, M.m, tc, 2);
+                });
+                B->tune_ms += 2 * ms;
+                if (ms < bt) { bt = ms; best = tc; }
+            }
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_proj[key] = best;
+        }
+        M.tc = best;
+    }
+    return cudaGetLastError() == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
+}
+
+extern "C" {
+
+int svdsc_batch_destroy(svdsc_batch *B)
+{
+    if (!B) return SVDSC_OK;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    for (auto &a : B->A) csr_free(&a);
+    for (auto &a : B->AT) csr_free(&a);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    cudaFreeHost(B->h_mats);
+    cudaFreeHost(B->h_prm);
+    cudaFree(B->d_mats);
+    cudaFree(B->d_order);
+    cudaFree(B->d_stats);
+    cudaFree(B->d_slots);
+    cudaFree(B->d_prm);
+    cudaFree(B->d_queue);
+    cudaFree(B->slot_mem);
+    cudaFree(B->out_mem);
+    if (B->stream) cudaStreamDestroy(B->stream);
+    delete B;
+    return SVDSC_OK;
+}
+
+int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const int *k, const int *p,
+                       const svdsc_options *opt, void *stream)
+{
+    (void)stream;
+    if (!out || nb < 1 || !As || !k) return SVDSC_ERR_ARG;
+    *out = nullptr;
+    if (opt && opt->precision != SVDSC_MIXED) return SVDSC_ERR_ARG;  // the batched form is the mixed one
+    for (int b = 0; b < nb; b++) {
+        const svdsc_matrix &a = As[b];
+        if (a.format != SVDSC_CSR || a.m < 1 || a.n < 1) return SVDSC_ERR_ARG;
+        const int pb = p ? p[b] : -1;
+        const int t = pb < 0 ? std::max(15, 3 * k[b]) : k[b] + pb;
+        if (k[b] < 1 || k[b] > kBMaxK || t < k[b] || t > kBMaxT || t > a.m || t + 1 > a.n) return SVDSC_ERR_SIZE;
+    }
+    svdsc_batch *B = new (std::nothrow) svdsc_batch();
+    if (!B) return SVDSC_ERR_NOMEM;
+    B->nb = nb;
+    int rc = SVDSC_OK;
+    int dev = 0, nsm = 0, occ = 0;
+    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        svdsc_batch_destroy(B);
+        return SVDSC_ERR_CUDA;
+    }
+    if (cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmBytes) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel, kBT, kSmBytes) != cudaSuccess || occ < 1) {
+        svdsc_batch_destroy(B);
+        return SVDSC_ERR_CUDA;
+    }
+    B->A.resize(nb);
+    B->AT.resize(nb);
+    B->hm.resize(nb);
+    int64_t mmax = 0, nmax = 0;
+    int tmax = 0;
+    for (int b = 0; b < nb && rc == SVDSC_OK; b++) {
+        rc = csr_prepare(&As[b], true, false, &B->A[b], &B->AT[b], B->stream);
+        BMat &M = B->hm[b];
+        memset(&M, 0, sizeof(M));
+        M.m = As[b].m; M.n = As[b].n; M.nnz = B->A[b].nnz;
+        M.k = k[b];
+        const int pb = p ? p[b] : -1;
+        M.t = pb < 0 ? std::max(15, 3 * k[b]) : k[b] + pb;
+        M.rp = B->A[b].row_ptr; M.col = B->A[b].col; M.val = B->A[b].val32;
+        M.rpT = B->AT[b].row_ptr; M.colT = B->AT[b].col; M.valT = B->AT[b].val32;
+        M.seed = (opt ? opt->seed : 0) + (uint64_t)b;
+        M.gA = 8; M.gAT = 8; M.tc = 1;
+        mmax = std::max(mmax, M.m);
+        nmax = std::max(nmax, M.n);
+        tmax = std::max(tmax, M.t);
+    }
+    if (rc) { svdsc_batch_destroy(B); return rc; }
+    B->nslots = std::min(nb, nsm * occ);
+    const int64_t ldu = (mmax + 63) & ~int64_t(63), ldv = (nmax + 63) & ~int64_t(63);
+    const int64_t cols = tmax + 2;
+    const size_t per_slot = sizeof(double) * (size_t)(2 * ldu * cols + 2 * ldv * cols + (tmax + 1) * (tmax + 1) + 64) +
+                            sizeof(float) * (size_t)(2 * ldu * cols + 2 * ldv * cols) + 4096;
+    std::vector<BSlot> slots(B->nslots);
+    if (cudaMalloc(&B->slot_mem, per_slot * B->nslots) != cudaSuccess) { svdsc_batch_destroy(B); return SVDSC_ERR_NOMEM; }
+    cudaMemsetAsync(B->slot_mem, 0, per_slot * B->nslots, B->stream);
+    for (int s = 0; s < B->nslots; s++) {
+        uint8_t *base = (uint8_t *)B->slot_mem + per_slot * s;
+        auto take = [&](size_t bytes) { uint8_t *p = base; base += (bytes + 255) & ~(size_t)255; return p; };
+        BSlot &S = slots[s];
+        S.ldu = ldu; S.ldv = ldv;
+        S.U0 = (double *)take(sizeof(double) * ldu * cols);
+        S.U1 = (double *)take(sizeof(double) * ldu * cols);
+        S.V0 = (double *)take(sizeof(double) * ldv * cols);
+        S.V1 = (double *)take(sizeof(double) * ldv * cols);
+        S.T = (double *)take(sizeof(double) * (tmax + 1) * (tmax + 1));
+        S.U32_0 = (float *)take(sizeof(float) * ldu * cols);
+        S.U32_1 = (float *)take(sizeof(float) * ldu * cols);
+        S.V32_0 = (float *)take(sizeof(float) * ldv * cols);
+        S.V32_1 = (float *)take(sizeof(float) * ldv * cols);
+    }
+    // work order: largest estimated cost first
+    std::vector<int> order(nb);
+    for (int b = 0; b < nb; b++) order[b] = b;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        auto cost = [&](int b) { const BMat &M = B->hm[b]; return (double)(M.m + M.n) * M.t * M.t + (double)M.nnz * M.t * 4; };
+        return cost(x) > cost(y);
+    });
+    bool ok = cudaMalloc(&B->d_mats, sizeof(BMat) * nb) == cudaSuccess &&
+              cudaMalloc(&B->d_order, sizeof(int) * nb) == cudaSuccess &&
+              cudaMalloc(&B->d_stats, sizeof(BStat) * nb) == cudaSuccess &&
+              cudaMalloc(&B->d_slots, sizeof(BSlot) * B->nslots) == cudaSuccess &&
+              cudaMalloc(&B->d_prm, sizeof(BParams)) == cudaSuccess &&
+              cudaMalloc(&B->d_queue, sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&B->h_mats, sizeof(BMat) * nb) == cudaSuccess &&
+              cudaMallocHost(&B->h_prm, sizeof(BParams)) == cudaSuccess;
+    if (!ok) { svdsc_batch_destroy(B); return SVDSC_ERR_NOMEM; }
+    cudaMemcpyAsync(B->d_order, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, B->stream);
+    cudaMemcpyAsync(B->d_slots, slots.data(), sizeof(BSlot) * B->nslots, cudaMemcpyHostToDevice, B->stream);
+    // device output staging (used when outputs go to the host)
+    size_t tot = 0;
+    B->out_off.resize(nb);
+    for (int b = 0; b < nb; b++) {
+        B->out_off[b] = tot;
+        tot += (size_t)B->hm[b].k * (B->hm[b].m + B->hm[b].n + 2);
+    }
+    if (cudaMalloc(&B->out_mem, sizeof(double) * std::max<size_t>(tot, 1)) != cudaSuccess) {
+        svdsc_batch_destroy(B);
+        return SVDSC_ERR_NOMEM;
+    }
+    // autotune (per shape class, cached process-wide)
+    {
+        double *ysc = nullptr, *wsc = nullptr;
+        float *x32 = nullptr;
+        const int64_t ldy = std::max(mmax, nmax) + 64;
+        if (cudaMalloc(&ysc, sizeof(double) * ldy * nsm) != cudaSuccess ||
+            cudaMalloc(&x32, sizeof(float) * ldy) != cudaSuccess ||
+            cudaMalloc(&wsc, sizeof(double) * (size_t)mmax * (tmax / 2 + 1) + 64) != cudaSuccess) {
+            cudaFree(ysc); cudaFree(x32); cudaFree(wsc);
+            svdsc_batch_destroy(B);
+            return SVDSC_ERR_NOMEM;
+        }
+        cudaMemsetAsync(x32, 0, sizeof(float) * ldy, B->stream);
+        cudaMemsetAsync(wsc, 0, sizeof(double) * (size_t)mmax * (tmax / 2 + 1) + 64, B->stream);
+        for (int b = 0; b < nb && rc == SVDSC_OK; b++) rc = tune_matrix(B, b, nsm, ysc, ldy, x32, wsc);
+        cudaStreamSynchronize(B->stream);
+        cudaFree(ysc); cudaFree(x32); cudaFree(wsc);
+    }
+    if (rc == SVDSC_OK && cudaStreamSynchronize(B->stream) != cudaSuccess) rc = SVDSC_ERR_CUDA;
+    if (rc) { svdsc_batch_destroy(B); return rc; }
+    *out = B;
+    return SVDSC_OK;
+}
+
+int svdsc_batch_solve(svdsc_batch *B, double tol, int maxit, double *const *S, double *const *U,
+                      double *const *V, double *const *res, int out_on_device, svdsc_info *infos)
+{
+    if (!B || !(tol > 0.0) || maxit < 1 || !S || !U || !V) return SVDSC_ERR_ARG;
+    const int nb = B->nb;
+    for (int b = 0; b < nb; b++) {
+        BMat &M = B->hm[b];
+        if (!S[b] || !U[b] || !V[b]) return SVDSC_ERR_ARG;
+        if (out_on_device) {
+            M.S = S[b]; M.U = U[b]; M.V = V[b];
+            M.res = res && res[b] ? res[b] : B->out_mem + B->out_off[b] + (size_t)M.k * (M.m + M.n + 1);
+        } else {
+            double *o = B->out_mem + B->out_off[b];
+            M.U = o; M.V = o + (size_t)M.k * M.m; M.S = M.V + (size_t)M.k * M.n; M.res = M.S + M.k;
+        }
+    }
+    memcpy(B->h_mats, B->hm.data(), sizeof(BMat) * nb);
+    B->h_prm->tol = tol;
+    B->h_prm->maxit = maxit;
+    B->h_prm->nb = nb;
+    if (!B->exec) {  // capture upload + reset + persistent launch once; replay afterwards
+        if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SVDSC_ERR_CUDA;
+        cudaMemcpyAsync(B->d_mats, B->h_mats, sizeof(BMat) * nb, cudaMemcpyHostToDevice, B->stream);
+        cudaMemcpyAsync(B->d_prm, B->h_prm, sizeof(BParams), cudaMemcpyHostToDevice, B->stream);
+        cudaMemsetAsync(B->d_queue, 0, sizeof(int), B->stream);
+        batched_kernel<<<B->nslots, kBT, kSmBytes, B->stream>>>(B->d_mats, B->d_order, B->d_stats, B->d_slots,
+                                                                B->d_prm, B->d_queue);
+        if (cudaStreamEndCapture(B->stream, &B->graph) != cudaSuccess) return SVDSC_ERR_CUDA;
+        if (cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess) return SVDSC_ERR_CUDA;
+    }
+    if (cudaGraphLaunch(B->exec, B->stream) != cudaSuccess) return SVDSC_ERR_CUDA;
+    std::vector<BStat> st(nb);
+    if (cudaMemcpyAsync(st.data(), B->d_stats, sizeof(BStat) * nb, cudaMemcpyDeviceToHost, B->stream) != cudaSuccess)
+        return SVDSC_ERR_CUDA;
+    if (!out_on_device) {
+        for (int b = 0; b < nb; b++) {
+            const BMat &M = B->hm[b];
+            cudaMemcpyAsync(U[b], M.U, sizeof(double) * M.m * M.k, cudaMemcpyDeviceToHost, B->stream);
+            cudaMemcpyAsync(V[b], M.V, sizeof(double) * M.n * M.k, cudaMemcpyDeviceToHost, B->stream);
+            cudaMemcpyAsync(S[b], M.S, sizeof(double) * M.k, cudaMemcpyDeviceToHost, B->stream);
+            if (res && res[b]) cudaMemcpyAsync(res[b], M.res, sizeof(double) * M.k, cudaMemcpyDeviceToHost, B->stream);
+        }
+    }
+    if (cudaStreamSynchronize(B->stream) != cudaSuccess) return SVDSC_ERR_CUDA;
+    int worst = SVDSC_OK;
+    for (int b = 0; b < nb; b++) {
+        if (infos) {
+            svdsc_info &I = infos[b];
+            memset(&I, 0, sizeof(I));
+            I.converged = st[b].converged; I.nconv = st[b].nconv; I.restarts = st[b].restarts;
+            I.breakdowns = st[b].breakdowns; I.n_matvec = st[b].n_matvec; I.n_steps = st[b].n_steps;
+            I.anorm_est = st[b].anorm; I.beta_t = st[b].beta_t; I.t = B->hm[b].t;
+            I.reserved = st[b].err;
+        }
+        if (st[b].err) worst = st[b].err;
+        else if (!st[b].converged && worst == SVDSC_OK) worst = SVDSC_NOT_CONVERGED;
+    }
+    return worst;
+}
+
+int svdsc_solve_batched(int nb, const svdsc_matrix *As, const int *k, const int *p, double tol, int maxit,
+                        double *const *S, double *const *U, double *const *V, double *const *res,
+                        int out_on_device, const svdsc_options *opt, svdsc_info *infos)
+{
+    svdsc_batch *B = nullptr;
+    int rc = svdsc_batch_create(&B, nb, As, k, p, opt, nullptr);
+    if (rc) return rc;
+    rc = svdsc_batch_solve(B, tol, maxit, S, U, V, res, out_on_device, infos);
+    svdsc_batch_destroy(B);
+    return rc;
+}
+
+int svdsc_batch_tuning(const svdsc_batch *B, int b, int *lanes_A, int *lanes_AT, int *gemv_cols, double *tune_ms)
+{
+    if (!B || b < 0 || b >= B->nb) return SVDSC_ERR_ARG;
+    if (lanes_A) *lanes_A = B->hm[b].gA;
+    if (lanes_AT) *lanes_AT = B->hm[b].gAT;
+    if (gemv_cols) *gemv_cols = B->hm[b].tc;
+    if (tune_ms) *tune_ms = B->tune_ms;
+    return SVDSC_OK;
+}
+
+}  // extern "C"

@@ -6,6 +6,27 @@
 
 namespace svdsc {
 
+// Counter-based N(0,1) of the method's random vectors: SplitMix64 (Steele,
+// Lea & Flood 2014) as the mixing function and the Box-Muller transform
+// (1958).  Element j of draw d under seed: key = mix(seed); c = 2 (d 2^32 + j);
+// U1, U2 from the top 53 bits of mix(key + c), mix(key + c + 1), offset by one
+// half; z = sqrt(-2 ln U1) cos(2 pi U2).
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double normal_draw(uint64_t key, uint64_t draw, uint64_t j)
+{
+    const uint64_t c = 2ull * ((draw << 32) + j);
+    const double u1 = ((double)(splitmix_mix(key + c) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double u2 = ((double)(splitmix_mix(key + c + 1ull) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
 // Device-side status block of one context (device memory, read by the host at
 // restart boundaries only).
 struct DevStatus {

@@ -297,28 +297,13 @@ void finalize(double *w, const Chunk &c, const double *Pn, double *T_entry, DevS
 }
 
 // ---------------------------------------------------------------- random draws
-// Counter-based N(0,1): SplitMix64 (Steele, Lea & Flood 2014) as the mixing
-// function and the Box-Muller transform (1958).  Element j of draw d under
-// seed: key = mix(seed); c = 2 (d 2^32 + j); U1, U2 from mix(key + c) and
-// mix(key + c + 1) (top 53 bits, offset by one half); z = sqrt(-2 ln U1) cos(2 pi U2).
-__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z)
-{
-    z += 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
 
 __global__ void rng_normal_kernel(uint64_t seed, uint64_t draw, int64_t len, double *x)
 {
     const uint64_t key = splitmix_mix(seed);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t c = 2ull * ((draw << 32) + (uint64_t)j);
-        const double u1 = ((double)(splitmix_mix(key + c) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-        const double u2 = ((double)(splitmix_mix(key + c + 1ull) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-        x[j] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
-    }
+         j += (int64_t)gridDim.x * blockDim.x)
+        x[j] = normal_draw(key, draw, (uint64_t)j);
 }
 
 void rng_normal_vec(uint64_t seed, uint64_t draw, int64_t len, double *x, cudaStream_t s)
