@@ -347,7 +347,7 @@ def run_batch(args, ws, rank):
                       "scale": args.scale, "matrices": count, "total_nnz": int(sum(a.nnz for a in mats)),
                       "l2": "inputs larger than L2 (no flush)"},
            "batch": {"converged": nconv, "restarts_mean": float(np.mean([i["restarts"] for i in infos])),
-                     "create_s": create_s, "generate_s": gen_s, "tuning": b.tuning(0),
+                     "create_s": create_s, "generate_s": gen_s, "tuning": b.tuning(0), "layout": b.layout(),
                      "plain_fp64_gpu_s_estimate": plain_est, "speedup_vs_plain_gpu": plain_est / wall,
                      "sigma_rel_err_vs_plain_fp64_max": max(errs), "plain_sample": len(sample)},
            "hbm": {"alg_gbs": gbs, "frac_of_measured": gbs / peaks["hbm_gbs"]},

@@ -90,7 +90,7 @@ typedef struct svdsc_options {
     int32_t timing;        /* 1: time every kernel launch with CUDA events (fills svdsc_info.ms) */
     uint64_t seed;
     int32_t restart_gemm;  /* 0: tensor cores (svdsc_gemm modes 0/1, default); 1: FP64 FMA on CUDA cores */
-    int32_t reserved;
+    int32_t batch_cluster; /* batched form: CTAs (one cluster) per matrix, 1, 2, 4 or 8; 0 = automatic */
 } svdsc_options;
 
 /* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
@@ -255,9 +255,9 @@ int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, int64_t ldw,
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent truncated SVDs (uneven shapes and k) solved
- * in ONE persistent kernel launch, replayed from a CUDA graph.  One CTA per SM
- * takes matrices from a work queue (largest estimated cost first) and runs
- * Alg. 2 for each from start to finish.  Precision is the mixed form (FP32
+ * in ONE persistent kernel launch, replayed from a CUDA graph.  Thread-block
+ * clusters (1-8 CTAs, see svdsc_batch_layout) take matrices from a work queue
+ * (largest estimated cost first) and run Alg. 2 for each from start to finish.  Precision is the mixed form (FP32
  * CSR values, FP32 SpMV and first CGS pass, FP64 second pass, norms, projected
  * SVD and residual test, FP32 restart GEMM); options.precision must be
  * SVDSC_MIXED.  Limits per matrix: CSR input, 1 <= k <= 48, t = k + p <= 80
@@ -287,6 +287,13 @@ int svdsc_batch_solve(svdsc_batch *b, double tol, int maxit, double *const *S, d
 /* The autotuner's choice for matrix i and the total tuning time. */
 int svdsc_batch_tuning(const svdsc_batch *b, int i, int *lanes_A, int *lanes_AT, int *gemv_cols,
                        double *tune_ms);
+
+/* CTAs per matrix (thread-block cluster size: the rows of A, A^T and of the
+ * bases are split across them) and the number of clusters of the persistent
+ * launch.  Automatic choice: the smallest power of two <= 8 for which the
+ * costliest matrix, run on one cluster, takes at most twice its share of the
+ * batch's estimated work. */
+int svdsc_batch_layout(const svdsc_batch *b, int *cluster_size, int *clusters);
 
 int svdsc_batch_destroy(svdsc_batch *b);
 

@@ -33,7 +33,7 @@ F64, F32 = 0, 1
 EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "svdsc_matvec",
            "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc",
            "svdsc_gemm", "svdsc_batch_create", "svdsc_batch_solve", "svdsc_batch_tuning",
-           "svdsc_batch_destroy", "svdsc_solve_batched")
+           "svdsc_batch_destroy", "svdsc_solve_batched", "svdsc_batch_layout")
 
 
 class SvdscMatrix(C.Structure):
@@ -46,7 +46,7 @@ class SvdscMatrix(C.Structure):
 
 class SvdscOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("timing", C.c_int32), ("seed", C.c_uint64),
-                ("restart_gemm", C.c_int32), ("reserved", C.c_int32)]
+                ("restart_gemm", C.c_int32), ("batch_cluster", C.c_int32)]
 
 
 NUM_PHASES = 8
@@ -99,6 +99,7 @@ def lib():
         L.svdsc_batch_tuning.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                          C.POINTER(dbl)]
         L.svdsc_batch_destroy.argtypes = [vp]
+        L.svdsc_batch_layout.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.svdsc_solve_batched.argtypes = [i32, C.POINTER(SvdscMatrix), vp, vp, dbl, i32, vp, vp, vp, vp,
                                           i32, C.POINTER(SvdscOptions), C.POINTER(SvdscInfo)]
         for name in EXPORTS:
@@ -307,17 +308,22 @@ def _csr_struct(A, keep):
 class Batch:
     """Many truncated SVDs in one persistent launch (svdsc_batch_*), mixed precision."""
 
-    def __init__(self, mats, k, p=None, seed: int = 0):
+    def __init__(self, mats, k, p=None, seed: int = 0, cluster: int = 0):
         keep = []
         nb = len(mats)
         arr = (SvdscMatrix * nb)(*[_csr_struct(a, keep) for a in mats])
         self.k = np.ascontiguousarray(k, dtype=np.int32)
         self.p = np.ascontiguousarray(p if p is not None else self.k, dtype=np.int32)
         self.shapes = [(int(a.m), int(a.n)) for a in mats]
-        opt = SvdscOptions(MIXED, 0, seed, 0, 0)
+        opt = SvdscOptions(MIXED, 0, seed, 0, cluster)
         self.handle = C.c_void_p()
         _check(lib().svdsc_batch_create(C.byref(self.handle), nb, arr, _ptr(self.k), _ptr(self.p),
                                         C.byref(opt), None), "svdsc_batch_create")
+
+    def layout(self):
+        a, b = C.c_int(), C.c_int()
+        _check(lib().svdsc_batch_layout(self.handle, C.byref(a), C.byref(b)), "svdsc_batch_layout")
+        return {"cluster_size": a.value, "clusters": b.value}
 
     def tuning(self, i):
         a, b, c, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()

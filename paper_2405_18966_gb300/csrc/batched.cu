@@ -1,13 +1,18 @@
 // Batched form: many independent truncated SVDs (uneven shapes and k) in ONE
-// persistent launch.  One CTA per SM takes matrices from an atomic work queue
-// (largest estimated cost first) and runs Alg. 2 of the svds-C paper for each
-// from start to finish: Lanczos bidiagonalization with CGS2 full
+// persistent launch.  A thread-block cluster of C CTAs (C = 1, 2, 4 or 8)
+// takes matrices from an atomic work queue (largest estimated cost first) and
+// runs Alg. 2 of the svds-C paper for each from start to finish; the rows of
+// A, A^T and of the Lanczos bases are split across the cluster's CTAs, and
+// every reduction (projection coefficients, norms, the sign rule's argmax) is
+// combined through distributed shared memory in a fixed rank order, so every
+// CTA takes the same decisions.  The steps are: Lanczos bidiagonalization with CGS2 full
 // re-orthogonalization, the projected SVD (one-sided Jacobi in shared memory),
 // the Eq. (4) residual test and the augmented restart, then the outputs.
 // Precision is the mixed form: FP32 CSR values, FP32 SpMV with FP32
 // accumulation, FP32 first CGS pass on FP32 basis shadows, FP64 second pass,
-// norms, projected SVD and residuals, FP32 restart GEMM.  A CTA synchronizes
-// only with itself, so nothing waits across CTAs.  The launch (with the
+// norms, projected SVD and residuals, FP32 restart GEMM.  CTAs synchronize
+// only inside their own cluster (hardware cluster barrier); clusters never
+// wait on one another.  The launch (with the
 // parameter upload and queue reset) is captured once in a CUDA graph and
 // replayed by every solve.  SpMV lanes-per-row and the GEMV-T column tile are
 // chosen per matrix-shape class by timing the candidates (autotuner below).
@@ -48,8 +53,8 @@ struct BStat {
     int err, svd_sweeps;
 };
 
-struct BSlot {
-    double *U0, *U1, *V0, *V1, *T;
+struct BSlot {   // one per cluster (bases), T one per CTA
+    double *U0, *U1, *V0, *V1;
     float *U32_0, *U32_1, *V32_0, *V32_1;
     int64_t ldu, ldv;
 };
@@ -58,6 +63,63 @@ struct BParams {
     double tol;
     int maxit, nb;
 };
+
+// ------------------------------------------------------------ cluster helpers
+__device__ __forceinline__ uint32_t cl_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cl_size()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cl_id()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+// all threads of every CTA of the cluster; orders shared and global memory
+// at cluster scope
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cl_map(const void *p, uint32_t rank)
+{
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return ra;
+}
+
+__device__ __forceinline__ double cl_ld(const double *p, uint32_t rank)
+{
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(cl_map(p, rank)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ long long cl_ld_i64(const long long *p, uint32_t rank)
+{
+    long long v;
+    asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(cl_map(p, rank)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int cl_ld_i32(const int *p, uint32_t rank)
+{
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(cl_map(p, rank)) : "memory");
+    return v;
+}
 
 // shared-memory layout (doubles)
 constexpr int kSmB = 0;                               // B: t x t (Jacobi columns)
@@ -68,7 +130,8 @@ constexpr int kSmRho = kSmUt + kBMaxT;                // rho (k)
 constexpr int kSmH = kSmRho + kBMaxT;                 // projection coefficients (t + 2)
 constexpr int kSmRed = kSmH + kBMaxT + 8;             // reductions (4 x warps)
 constexpr int kSmSig = kSmRed + 4 * kBW;              // unsorted sigma (t)
-constexpr int kSmDoubles = kSmSig + kBMaxT;
+constexpr int kSmPart = kSmSig + kBMaxT;               // cluster partials: 2 x (t + 8)
+constexpr int kSmDoubles = kSmPart + 2 * (kBMaxT + 8);
 // floats after the doubles: Q_U (t x k), Q_V (t x k), h32 (t + 2)
 constexpr int kSmQU = 0;
 constexpr int kSmQV = kSmQU + kBMaxT * kBMaxK;
@@ -265,54 +328,111 @@ struct BRun {
     double *U, *V, *Ua, *Va, *T;
     float *U32, *V32, *U32a, *V32a;
     int64_t ldu, ldv, m, n;
+    int64_t m0, m1, n0, n1;   // this CTA's rows of the u-side and v-side vectors
     int t, k, tc;
+    uint32_t rank, csize;
+    int phase;                 // which partial buffer the next cluster reduction uses
     uint64_t key, draws;
     double anorm;
     double *sm;
     float *smf;
     bool failed;
+    bool lead;                 // rank 0 of the cluster writes the per-matrix outputs
 };
 
 __device__ __forceinline__ double *Tb(BRun &R, int r, int c) { return R.T + r + (int64_t)c * (R.t + 1); }
 
+// The partial buffer the next reduction writes into.
+__device__ __forceinline__ double *part_buf(BRun &R) { return R.sm + kSmPart + R.phase * (kBMaxT + 8); }
+
+// Cluster reduction: every CTA wrote `cnt` partial values into part_buf(R);
+// out[c] = sum over ranks (in rank order) of those values, identical in every
+// CTA.  Double-buffered: one cluster barrier per reduction suffices, because a
+// buffer is rewritten only after a later barrier that every CTA reached after
+// reading it.
+__device__ void cl_gather(BRun &R, int cnt, double *out)
+{
+    const double *buf = part_buf(R);
+    __syncthreads();
+    cl_sync();
+    for (int c = threadIdx.x; c < cnt; c += kBT) {
+        double s = 0.0;
+        for (uint32_t q = 0; q < R.csize; q++) s += cl_ld(buf + c, q);
+        out[c] = s;
+    }
+    R.phase ^= 1;
+    __syncthreads();
+}
+
+__device__ double cl_sum_scalar(BRun &R, double v)
+{
+    double *buf = part_buf(R);
+    if (threadIdx.x == 0) buf[0] = v;
+    double *tmp = R.sm + kSmRed + 2 * kBW;
+    cl_gather(R, 1, tmp);
+    return tmp[0];
+}
+
+// CGS2 of the column w (this CTA's rows [r0, r1)) against ncols columns:
+// pass 1 on the FP32 shadow, pass 2 in FP64.  Returns the cluster-wide ||w||^2.
+__device__ double cl_cgs2(BRun &R, const double *W, const float *W32, int64_t ld, int ncols, double *w,
+                          int64_t r0, int64_t r1)
+{
+    double *red = R.sm + kSmRed, *h = R.sm + kSmH;
+    float *h32 = R.smf + kSmH32;
+    const int64_t len = r1 - r0;
+    if (ncols <= 0) return cl_sum_scalar(R, cta_norm2(w + r0, len, red));
+    cta_proj<float>(R.tc, W32 + r0, ld, ncols, w + r0, len, part_buf(R));
+    cl_gather(R, ncols, h);
+    for (int c = threadIdx.x; c < ncols; c += kBT) h32[c] = (float)h[c];
+    __syncthreads();
+    cta_update<float, float>(W32 + r0, ld, ncols, h32, w + r0, len, false, red);
+    cta_proj<double>(R.tc, W + r0, ld, ncols, w + r0, len, part_buf(R));
+    cl_gather(R, ncols, h);
+    return cl_sum_scalar(R, cta_update<double, double>(W + r0, ld, ncols, h, w + r0, len, true, red));
+}
+
 // Normalises the freshly orthogonalized column `col` of side (0: U, 1: V);
 // a breakdown (norm <= 1e-13 * largest alpha/beta/sigma so far) draws random
-// replacement vectors.  Returns the T entry (0 after a breakdown).
+// replacement vectors.  Returns the T entry (0 after a breakdown).  Ends with
+// a cluster barrier so every CTA sees the whole vector.
 __device__ double finish_vector(BRun &R, int side, int col, double nrm2)
 {
-    const int64_t len = side ? R.n : R.m;
+    const int64_t r0 = side ? R.n0 : R.m0, r1 = side ? R.n1 : R.m1;
     double *W = side ? R.V : R.U;
     float *W32 = side ? R.V32 : R.U32;
     const int64_t ld = side ? R.ldv : R.ldu;
     double *w = W + (int64_t)col * ld;
     float *w32 = W32 + (int64_t)col * ld;
-    double *red = R.sm + kSmRed;
     const double nrm = sqrt(nrm2);
+    double out = 0.0;
     if (!isfinite(nrm)) {
         R.failed = true;
-        if (threadIdx.x == 0) R.st->err = SVDSC_ERR_NONFINITE;
-        return 0.0;
-    }
-    if (nrm > 1e-13 * R.anorm) {
+        if (threadIdx.x == 0 && R.lead) R.st->err = SVDSC_ERR_NONFINITE;
+    } else if (nrm > 1e-13 * R.anorm) {
         if (nrm > R.anorm) R.anorm = nrm;
-        cta_scale(w, w32, len, 1.0 / nrm);
-        return nrm;
-    }
-    if (threadIdx.x == 0) R.st->breakdowns++;
-    for (int attempt = 0; attempt < 8; attempt++) {
-        const uint64_t d = R.draws++;
-        for (int64_t j = threadIdx.x; j < len; j += kBT) w[j] = normal_draw(R.key, d, (uint64_t)j);
-        __syncthreads();
-        const double n2 = cta_cgs2(R.tc, W, W32, ld, col, w, len, R.sm + kSmH, R.smf + kSmH32, red);
-        const double nr = sqrt(n2);
-        if (nr > 1e-8 && isfinite(nr)) {
-            cta_scale(w, w32, len, 1.0 / nr);
-            return 0.0;
+        cta_scale(w + r0, w32 + r0, r1 - r0, 1.0 / nrm);
+        out = nrm;
+    } else {
+        if (threadIdx.x == 0 && R.lead) R.st->breakdowns++;
+        bool done = false;
+        for (int attempt = 0; attempt < 8 && !done; attempt++) {
+            const uint64_t d = R.draws++;
+            for (int64_t j = r0 + threadIdx.x; j < r1; j += kBT) w[j] = normal_draw(R.key, d, (uint64_t)j);
+            __syncthreads();
+            const double nr = sqrt(cl_cgs2(R, W, W32, ld, col, w, r0, r1));
+            if (nr > 1e-8 && isfinite(nr)) {
+                cta_scale(w + r0, w32 + r0, r1 - r0, 1.0 / nr);
+                done = true;
+            }
+        }
+        if (!done) {
+            for (int64_t j = r0 + threadIdx.x; j < r1; j += kBT) { w[j] = 0.0; w32[j] = 0.f; }
+            __syncthreads();
         }
     }
-    for (int64_t j = threadIdx.x; j < len; j += kBT) { w[j] = 0.0; w32[j] = 0.f; }
-    __syncthreads();
-    return 0.0;
+    cl_sync();
+    return out;
 }
 
 // Alg. 1 for iterations i = s..t (u_{t+1} not formed)
@@ -320,33 +440,34 @@ __device__ void lbp_from(BRun &R, int s)
 {
     const BMat &M = *R.M;
     double *red = R.sm + kSmRed;
+    (void)red;
     for (int i = s; i <= R.t && !R.failed; i++) {
         // v_{i+1} = A^T u_i - alpha_i v_i, CGS2 against v_1..v_i
         double *vout = R.V + (int64_t)i * R.ldv;
-        cta_spmv(M.gAT, M.rpT, M.colT, M.valT, R.U32 + (int64_t)(i - 1) * R.ldu, R.n,
-                 R.V + (int64_t)(i - 1) * R.ldv, *Tb(R, i - 1, i - 1), vout);
-        double n2 = cta_cgs2(R.tc, R.V, R.V32, R.ldv, i, vout, R.n, R.sm + kSmH, R.smf + kSmH32, red);
+        cta_spmv(M.gAT, M.rpT + R.n0, M.colT, M.valT, R.U32 + (int64_t)(i - 1) * R.ldu, R.n1 - R.n0,
+                 R.V + (int64_t)(i - 1) * R.ldv + R.n0, *Tb(R, i - 1, i - 1), vout + R.n0);
+        double n2 = cl_cgs2(R, R.V, R.V32, R.ldv, i, vout, R.n0, R.n1);
         const double beta = finish_vector(R, 1, i, n2);
         if (threadIdx.x == 0) *Tb(R, i - 1, i) = beta;
         __syncthreads();
-        if (threadIdx.x == 0) { R.st->n_matvec++; R.st->n_steps++; }
+        if (threadIdx.x == 0 && R.lead) { R.st->n_matvec++; R.st->n_steps++; }
         if (i == R.t) break;
         // u_{i+1} = A v_{i+1} - beta_i u_i, CGS2 against u_1..u_i
         double *uout = R.U + (int64_t)i * R.ldu;
-        cta_spmv(M.gA, M.rp, M.col, M.val, R.V32 + (int64_t)i * R.ldv, R.m, R.U + (int64_t)(i - 1) * R.ldu,
-                 beta, uout);
-        n2 = cta_cgs2(R.tc, R.U, R.U32, R.ldu, i, uout, R.m, R.sm + kSmH, R.smf + kSmH32, red);
+        cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32 + (int64_t)i * R.ldv, R.m1 - R.m0,
+                 R.U + (int64_t)(i - 1) * R.ldu + R.m0, beta, uout + R.m0);
+        n2 = cl_cgs2(R, R.U, R.U32, R.ldu, i, uout, R.m0, R.m1);
         const double alpha = finish_vector(R, 0, i, n2);
         if (threadIdx.x == 0) *Tb(R, i, i) = alpha;
         __syncthreads();
-        if (threadIdx.x == 0) { R.st->n_matvec++; R.st->n_steps++; }
+        if (threadIdx.x == 0 && R.lead) { R.st->n_matvec++; R.st->n_steps++; }
     }
 }
 
 // Projected SVD of T(1:t,1:t) by one-sided Jacobi in shared memory (FP64,
-// round-robin pairs, one warp per pair).  Leaves the descending sigma in
-// sm[kSmS], Uh(t, j) in sm[kSmUt] and the leading k columns of Uh and Vh (as
-// FP32) in the Q buffers.
+// round-robin pairs, one warp per pair), computed by every CTA of the cluster
+// on identical input.  Leaves the descending sigma in sm[kSmS], Uh(t, j) in
+// sm[kSmUt] and the leading k columns of Uh and Vh (as FP32) in the Q buffers.
 __device__ void cta_small_svd(BRun &R)
 {
     const int t = R.t, k = R.k;
@@ -430,7 +551,7 @@ __device__ void cta_small_svd(BRun &R)
             }
     }
     __syncthreads();
-    if (threadIdx.x == 0) R.st->svd_sweeps = conv ? sweeps : -1;
+    if (threadIdx.x == 0 && R.lead) R.st->svd_sweeps = conv ? sweeps : -1;
 }
 
 // C (rows x k) = W32 (rows x t) Q (t x k, FP32 in shared memory), FP32 FMA;
@@ -458,16 +579,17 @@ __device__ void cta_gemm32(const float *__restrict__ W32, int64_t ld, int64_t ro
     __syncthreads();
 }
 
-// sign rule: v_j's largest-magnitude entry (lowest index on ties) positive
-__device__ void cta_sign(double *U, int64_t m, double *V, int64_t n, int k, double *red)
+// sign rule: v_j's largest-magnitude entry (lowest index on ties) positive;
+// the argmax is combined over the cluster in rank order.
+__device__ void cl_sign(BRun &R, double *U, int64_t ldU, double *V, int64_t ldV)
 {
     __shared__ double sb[kBW];
     __shared__ int64_t si[kBW];
-    for (int j = 0; j < k; j++) {
-        double *v = V + (int64_t)j * n;
+    for (int j = 0; j < R.k; j++) {
+        double *v = V + (int64_t)j * ldV;
         double best = -1.0;
-        int64_t bi = 0;
-        for (int64_t r = threadIdx.x; r < n; r += kBT) {
+        int64_t bi = R.n0;
+        for (int64_t r = R.n0 + threadIdx.x; r < R.n1; r += kBT) {
             const double a = fabs(v[r]);
             if (a > best) { best = a; bi = r; }
         }
@@ -479,30 +601,50 @@ __device__ void cta_sign(double *U, int64_t m, double *V, int64_t n, int k, doub
         __syncthreads();
         if ((threadIdx.x & 31) == 0) { sb[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = bi; }
         __syncthreads();
-        double bb = sb[0];
-        int64_t ii = si[0];
-        for (int w = 1; w < kBW; w++)
-            if (sb[w] > bb || (sb[w] == bb && si[w] < ii)) { bb = sb[w]; ii = si[w]; }
-        const bool flip = v[ii] < 0.0;
+        double *buf = part_buf(R);
+        if (threadIdx.x == 0) {
+            double bb = sb[0];
+            int64_t ii = si[0];
+            for (int w = 1; w < kBW; w++)
+                if (sb[w] > bb || (sb[w] == bb && si[w] < ii)) { bb = sb[w]; ii = si[w]; }
+            buf[0] = bb;
+            buf[1] = (double)ii;
+            buf[2] = (ii >= R.n0 && ii < R.n1) ? v[ii] : 0.0;
+        }
         __syncthreads();
-        if (flip) {
-            for (int64_t r = threadIdx.x; r < n; r += kBT) v[r] = -v[r];
-            double *u = U + (int64_t)j * m;
-            for (int64_t r = threadIdx.x; r < m; r += kBT) u[r] = -u[r];
+        cl_sync();
+        double bb = -2.0, val = 0.0;
+        int64_t ii = 0;
+        for (uint32_t q = 0; q < R.csize; q++) {
+            const double b2 = cl_ld(buf, q);
+            const int64_t i2 = (int64_t)cl_ld(buf + 1, q);
+            if (b2 > bb || (b2 == bb && i2 < ii)) { bb = b2; ii = i2; val = cl_ld(buf + 2, q); }
+        }
+        R.phase ^= 1;
+        if (val < 0.0) {
+            for (int64_t r = R.n0 + threadIdx.x; r < R.n1; r += kBT) v[r] = -v[r];
+            double *u = U + (int64_t)j * ldU;
+            for (int64_t r = R.m0 + threadIdx.x; r < R.m1; r += kBT) u[r] = -u[r];
         }
         __syncthreads();
     }
-    (void)red;
 }
 
-__device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, const BParams &P, double *sm, float *smf)
+__device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *Tpriv, const BParams &P,
+                          double *sm, float *smf, int &phase)
 {
     BRun R;
     R.M = &M;
     R.st = st;
-    R.U = slot.U0; R.Ua = slot.U1; R.V = slot.V0; R.Va = slot.V1; R.T = slot.T;
+    R.U = slot.U0; R.Ua = slot.U1; R.V = slot.V0; R.Va = slot.V1; R.T = Tpriv;
     R.U32 = slot.U32_0; R.U32a = slot.U32_1; R.V32 = slot.V32_0; R.V32a = slot.V32_1;
     R.ldu = slot.ldu; R.ldv = slot.ldv; R.m = M.m; R.n = M.n; R.t = M.t; R.k = M.k; R.tc = M.tc;
+    R.rank = cl_rank();
+    R.csize = cl_size();
+    R.lead = R.rank == 0;
+    R.m0 = M.m * R.rank / R.csize; R.m1 = M.m * (R.rank + 1) / R.csize;
+    R.n0 = M.n * R.rank / R.csize; R.n1 = M.n * (R.rank + 1) / R.csize;
+    R.phase = phase;
     R.key = splitmix_mix(M.seed);
     R.draws = 0;
     R.anorm = 0.0;
@@ -511,24 +653,26 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, const BPa
     R.failed = false;
     double *red = sm + kSmRed;
     const int t = R.t, k = R.k;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && R.lead) {
         st->converged = 0; st->nconv = 0; st->restarts = 0; st->breakdowns = 0;
         st->n_matvec = 0; st->n_steps = 0; st->err = 0; st->svd_sweeps = 0;
     }
     for (int64_t i = threadIdx.x; i < (int64_t)(t + 1) * (t + 1); i += kBT) R.T[i] = 0.0;
     // v_1: draw 0, normalised
-    for (int64_t j = threadIdx.x; j < R.n; j += kBT) R.V[j] = normal_draw(R.key, 0, (uint64_t)j);
+    for (int64_t j = R.n0 + threadIdx.x; j < R.n1; j += kBT) R.V[j] = normal_draw(R.key, 0, (uint64_t)j);
     R.draws = 1;
     __syncthreads();
     {
-        const double nv = sqrt(cta_norm2(R.V, R.n, red));
-        cta_scale(R.V, R.V32, R.n, 1.0 / nv);
+        const double nv = sqrt(cl_sum_scalar(R, cta_norm2(R.V + R.n0, R.n1 - R.n0, red)));
+        cta_scale(R.V + R.n0, R.V32 + R.n0, R.n1 - R.n0, 1.0 / nv);
+        cl_sync();
     }
     // u_1 = A v_1, alpha_1
-    cta_spmv(M.gA, M.rp, M.col, M.val, R.V32, R.m, nullptr, 0.0, R.U);
+    cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32, R.m1 - R.m0, nullptr, 0.0, R.U + R.m0);
     {
-        const double a1 = finish_vector(R, 0, 0, cta_norm2(R.U, R.m, red));
-        if (threadIdx.x == 0) { *Tb(R, 0, 0) = a1; st->n_matvec++; st->n_steps++; }
+        const double a1 = finish_vector(R, 0, 0, cl_sum_scalar(R, cta_norm2(R.U + R.m0, R.m1 - R.m0, red)));
+        if (threadIdx.x == 0) *Tb(R, 0, 0) = a1;
+        if (threadIdx.x == 0 && R.lead) { st->n_matvec++; st->n_steps++; }
         __syncthreads();
     }
     lbp_from(R, 1);
@@ -548,16 +692,16 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, const BPa
         if (threadIdx.x < k) {
             const int j = threadIdx.x;
             const double den = S[j] > DBL_EPSILON * S[0] ? S[j] : DBL_EPSILON * S[0];
-            M.res[j] = den > 0.0 ? fabs(beta_t * ut[j]) / den : 0.0;
+            if (R.lead) M.res[j] = den > 0.0 ? fabs(beta_t * ut[j]) / den : 0.0;
             rho[j] = beta_t * ut[j];
         }
-        if (threadIdx.x == 0) { st->nconv = nconv; st->converged = (nconv == k); st->beta_t = beta_t; }
+        if (threadIdx.x == 0 && R.lead) { st->nconv = nconv; st->converged = (nconv == k); st->beta_t = beta_t; }
         __syncthreads();
         if (nconv == k || it == P.maxit) break;
-        // augmented restart: U~ = U(:,1:t) Uh(:,1:k), V~ = V(:,1:t) Vh(:,1:k) into the spare bases
-        cta_gemm32(R.U32, R.ldu, R.m, t, R.smf + kSmQU, k, R.Ua, R.U32a, R.ldu);
-        cta_gemm32(R.V32, R.ldv, R.n, t, R.smf + kSmQV, k, R.Va, R.V32a, R.ldv);
-        for (int64_t j = threadIdx.x; j < R.n; j += kBT) {  // v_{k+1} = v_{t+1}
+        // augmented restart: this CTA's rows of U~ = U(:,1:t) Uh(:,1:k), V~ = V(:,1:t) Vh(:,1:k)
+        cta_gemm32(R.U32 + R.m0, R.ldu, R.m1 - R.m0, t, R.smf + kSmQU, k, R.Ua + R.m0, R.U32a + R.m0, R.ldu);
+        cta_gemm32(R.V32 + R.n0, R.ldv, R.n1 - R.n0, t, R.smf + kSmQV, k, R.Va + R.n0, R.V32a + R.n0, R.ldv);
+        for (int64_t j = R.n0 + threadIdx.x; j < R.n1; j += kBT) {  // v_{k+1} = v_{t+1}
             R.Va[j + (int64_t)k * R.ldv] = R.V[j + (int64_t)t * R.ldv];
             R.V32a[j + (int64_t)k * R.ldv] = R.V32[j + (int64_t)t * R.ldv];
         }
@@ -575,45 +719,55 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, const BPa
             *Tb(R, j, k) = rho[j];
         }
         __syncthreads();
+        cl_sync();  // v_{k+1} complete on every CTA before the product reads it
         // u_{k+1} = A v_{k+1} - U~ rho (Eq. 7), CGS2 against U~
         double *uk = R.U + (int64_t)k * R.ldu;
-        cta_spmv(M.gA, M.rp, M.col, M.val, R.V32 + (int64_t)k * R.ldv, R.m, nullptr, 0.0, uk);
-        cta_update<double, double>(R.U, R.ldu, k, rho, uk, R.m, false, red);
-        const double n2 = cta_cgs2(R.tc, R.U, R.U32, R.ldu, k, uk, R.m, sm + kSmH, smf + kSmH32, red);
+        cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32 + (int64_t)k * R.ldv, R.m1 - R.m0, nullptr, 0.0, uk + R.m0);
+        cta_update<double, double>(R.U + R.m0, R.ldu, k, rho, uk + R.m0, R.m1 - R.m0, false, red);
+        const double n2 = cl_cgs2(R, R.U, R.U32, R.ldu, k, uk, R.m0, R.m1);
         const double ak = finish_vector(R, 0, k, n2);
-        if (threadIdx.x == 0) { *Tb(R, k, k) = ak; st->n_matvec++; st->n_steps++; }
+        if (threadIdx.x == 0) *Tb(R, k, k) = ak;
+        if (threadIdx.x == 0 && R.lead) { st->n_matvec++; st->n_steps++; }
         __syncthreads();
         restarts++;
-        if (threadIdx.x == 0) st->restarts = restarts;
+        if (threadIdx.x == 0 && R.lead) st->restarts = restarts;
         lbp_from(R, k + 1);
     }
-    if (R.failed) return;
-    // outputs: S, U = U(:,1:t) Uh(:,1:k), V = V(:,1:t) Vh(:,1:k), sign rule
-    for (int j = threadIdx.x; j < k; j += kBT) M.S[j] = sm[kSmS + j];
-    cta_gemm32(R.U32, R.ldu, R.m, t, smf + kSmQU, k, M.U, nullptr, R.m);
-    cta_gemm32(R.V32, R.ldv, R.n, t, smf + kSmQV, k, M.V, nullptr, R.n);
-    cta_sign(M.U, R.m, M.V, R.n, k, red);
-    if (threadIdx.x == 0) st->anorm = R.anorm;
+    if (!R.failed) {
+        // outputs: S, this CTA's rows of U = U(:,1:t) Uh(:,1:k), V = V(:,1:t) Vh(:,1:k), sign rule
+        if (R.lead)
+            for (int j = threadIdx.x; j < k; j += kBT) M.S[j] = sm[kSmS + j];
+        cta_gemm32(R.U32 + R.m0, R.ldu, R.m1 - R.m0, t, smf + kSmQU, k, M.U + R.m0, nullptr, R.m);
+        cta_gemm32(R.V32 + R.n0, R.ldv, R.n1 - R.n0, t, smf + kSmQV, k, M.V + R.n0, nullptr, R.n);
+        cl_sign(R, M.U, R.m, M.V, R.n);
+        if (threadIdx.x == 0 && R.lead) st->anorm = R.anorm;
+    }
+    phase = R.phase;
 }
 
 __global__ void __launch_bounds__(kBT, 1)
 batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, BStat *stats,
-               const BSlot *__restrict__ slots, const BParams *prm, int *queue)
+               const BSlot *__restrict__ slots, double *Tall, int64_t tstride, const BParams *prm, int *queue)
 {
     extern __shared__ __align__(16) double bsm[];
     double *sm = bsm;
     float *smf = (float *)(bsm + kSmDoubles);
     __shared__ int item;
-    const BSlot slot = slots[blockIdx.x];
+    const BSlot slot = slots[cl_id()];
+    double *Tpriv = Tall + (int64_t)blockIdx.x * tstride;
     const BParams P = *prm;
+    int phase = 0;
     while (true) {
         __syncthreads();
-        if (threadIdx.x == 0) item = atomicAdd(queue, 1);
+        cl_sync();  // every CTA has read the previous item
+        if (threadIdx.x == 0 && cl_rank() == 0) item = atomicAdd(queue, 1);
         __syncthreads();
-        const int it = item;
+        cl_sync();
+        const int it = cl_ld_i32(&item, 0);
+        cl_sync();  // no CTA leaves while another still reads its shared memory
         if (it >= P.nb) break;
         const int b = order[it];
-        solve_one(mats[b], stats + b, slot, P, sm, smf);
+        solve_one(mats[b], stats + b, slot, Tpriv, P, sm, smf, phase);
     }
 }
 
@@ -657,6 +811,9 @@ struct svdsc_batch {
     BParams *d_prm = nullptr;
     int *d_queue = nullptr;
     void *slot_mem = nullptr;
+    double *d_T = nullptr;       // one projected matrix per CTA
+    int64_t tstride = 0;
+    int csize = 1;               // CTAs per cluster (per matrix)
     double *out_mem = nullptr;   // device outputs when the caller wants host outputs
     std::vector<size_t> out_off;
     cudaGraph_t graph = nullptr;
@@ -764,6 +921,7 @@ int svdsc_batch_destroy(svdsc_batch *B)
     cudaFree(B->d_prm);
     cudaFree(B->d_queue);
     cudaFree(B->slot_mem);
+    cudaFree(B->d_T);
     cudaFree(B->out_mem);
     if (B->stream) cudaStreamDestroy(B->stream);
     delete B;
@@ -823,14 +981,50 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
         tmax = std::max(tmax, M.t);
     }
     if (rc) { svdsc_batch_destroy(B); return rc; }
-    B->nslots = std::min(nb, nsm * occ);
+    // cluster size: the smallest power of two (<= 8) for which the costliest
+    // matrix on its cluster is not the bottleneck of the whole batch
+    auto est_cost = [&](int b) {
+        const BMat &M = B->hm[b];
+        return (double)(M.m + M.n) * M.t * M.t + 4.0 * (double)M.nnz * M.t;
+    };
+    double total = 0.0, worst = 0.0;
+    for (int b = 0; b < nb; b++) { total += est_cost(b); worst = std::max(worst, est_cost(b)); }
+    int C = 1;
+    while (C < 8 && worst * nsm > 2.0 * total * C) C *= 2;
+    if (opt && opt->batch_cluster > 0) C = opt->batch_cluster;  // explicit: 1, 2, 4 or 8
+    if (C != 1 && C != 2 && C != 4 && C != 8) { svdsc_batch_destroy(B); return SVDSC_ERR_ARG; }
+    B->csize = C;
+    {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(C * 64);
+        cfg.blockDim = dim3(kBT);
+        cfg.dynamicSmemBytes = kSmBytes;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, batched_kernel, &cfg) != cudaSuccess || ncl < 1) {
+            svdsc_batch_destroy(B);
+            return SVDSC_ERR_CUDA;
+        }
+        B->nslots = std::min(nb, ncl);  // clusters in the persistent grid
+    }
     const int64_t ldu = (mmax + 63) & ~int64_t(63), ldv = (nmax + 63) & ~int64_t(63);
     const int64_t cols = tmax + 2;
-    const size_t per_slot = sizeof(double) * (size_t)(2 * ldu * cols + 2 * ldv * cols + (tmax + 1) * (tmax + 1) + 64) +
+    const size_t per_slot = sizeof(double) * (size_t)(2 * ldu * cols + 2 * ldv * cols + 64) +
                             sizeof(float) * (size_t)(2 * ldu * cols + 2 * ldv * cols) + 4096;
     std::vector<BSlot> slots(B->nslots);
     if (cudaMalloc(&B->slot_mem, per_slot * B->nslots) != cudaSuccess) { svdsc_batch_destroy(B); return SVDSC_ERR_NOMEM; }
     cudaMemsetAsync(B->slot_mem, 0, per_slot * B->nslots, B->stream);
+    B->tstride = ((int64_t)(tmax + 1) * (tmax + 1) + 31) & ~int64_t(31);
+    if (cudaMalloc(&B->d_T, sizeof(double) * B->tstride * B->nslots * C) != cudaSuccess) {
+        svdsc_batch_destroy(B);
+        return SVDSC_ERR_NOMEM;
+    }
     for (int s = 0; s < B->nslots; s++) {
         uint8_t *base = (uint8_t *)B->slot_mem + per_slot * s;
         auto take = [&](size_t bytes) { uint8_t *p = base; base += (bytes + 255) & ~(size_t)255; return p; };
@@ -840,7 +1034,6 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
         S.U1 = (double *)take(sizeof(double) * ldu * cols);
         S.V0 = (double *)take(sizeof(double) * ldv * cols);
         S.V1 = (double *)take(sizeof(double) * ldv * cols);
-        S.T = (double *)take(sizeof(double) * (tmax + 1) * (tmax + 1));
         S.U32_0 = (float *)take(sizeof(float) * ldu * cols);
         S.U32_1 = (float *)take(sizeof(float) * ldu * cols);
         S.V32_0 = (float *)take(sizeof(float) * ldv * cols);
@@ -924,8 +1117,20 @@ int svdsc_batch_solve(svdsc_batch *B, double tol, int maxit, double *const *S, d
         cudaMemcpyAsync(B->d_mats, B->h_mats, sizeof(BMat) * nb, cudaMemcpyHostToDevice, B->stream);
         cudaMemcpyAsync(B->d_prm, B->h_prm, sizeof(BParams), cudaMemcpyHostToDevice, B->stream);
         cudaMemsetAsync(B->d_queue, 0, sizeof(int), B->stream);
-        batched_kernel<<<B->nslots, kBT, kSmBytes, B->stream>>>(B->d_mats, B->d_order, B->d_stats, B->d_slots,
-                                                                B->d_prm, B->d_queue);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = B->csize;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(B->nslots * B->csize);
+        cfg.blockDim = dim3(kBT);
+        cfg.dynamicSmemBytes = kSmBytes;
+        cfg.stream = B->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, batched_kernel, (const BMat *)B->d_mats, (const int *)B->d_order, B->d_stats,
+                           (const BSlot *)B->d_slots, B->d_T, B->tstride, (const BParams *)B->d_prm, B->d_queue);
         if (cudaStreamEndCapture(B->stream, &B->graph) != cudaSuccess) return SVDSC_ERR_CUDA;
         if (cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess) return SVDSC_ERR_CUDA;
     }
@@ -978,6 +1183,14 @@ int svdsc_batch_tuning(const svdsc_batch *B, int b, int *lanes_A, int *lanes_AT,
     if (lanes_AT) *lanes_AT = B->hm[b].gAT;
     if (gemv_cols) *gemv_cols = B->hm[b].tc;
     if (tune_ms) *tune_ms = B->tune_ms;
+    return SVDSC_OK;
+}
+
+int svdsc_batch_layout(const svdsc_batch *B, int *cluster_size, int *clusters)
+{
+    if (!B) return SVDSC_ERR_ARG;
+    if (cluster_size) *cluster_size = B->csize;
+    if (clusters) *clusters = B->nslots;
     return SVDSC_OK;
 }
 

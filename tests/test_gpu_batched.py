@@ -24,11 +24,15 @@ def _fp64_copy(a):
     return synth.CSR(a.m, a.n, a.row_ptr, a.col_idx, a.values.astype(np.float64))
 
 
-def test_batched_uneven_shapes_vs_oracle(pkg, orc):
+@pytest.mark.parametrize("cluster", [0, 1, 2, 8])
+def test_batched_uneven_shapes_vs_oracle(pkg, orc, cluster):
+    """cluster = CTAs per matrix (0: automatic); rows split across the cluster."""
     items = synth.workload_batch(count=10, size_scale=0.08, seed=7)
     mats = [it.a for it in items]
     ks = [it.k for it in items]
-    b = pkg.Batch(mats, ks, ks, seed=3)
+    b = pkg.Batch(mats, ks, ks, seed=3, cluster=cluster)
+    if cluster:
+        assert b.layout()["cluster_size"] == cluster
     out = b.solve(1e-10, 200)
     for i, it in enumerate(items):
         info = out["infos"][i]
