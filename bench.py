@@ -390,8 +390,8 @@ def run_kernel(args):
         t = args.ncols
         s.reserve(t)
         Wc = torch.randn((t, m), dtype=torch.float64, device="cuda", generator=g) / np.sqrt(m)  # column-major m x t
-        Qc = torch.linalg.qr(torch.randn((t, t), dtype=torch.float64, device="cuda", generator=g))[0][:k, :]
-        Qc = Qc.contiguous()  # column-major t x k (rows of Qc are columns)
+        q0 = np.linalg.qr(np.random.default_rng(0).standard_normal((t, t)))[0]
+        Qc = torch.tensor(np.ascontiguousarray(q0[:k, :]), device="cuda")  # column-major t x k
         Cc = torch.empty((k, m), dtype=torch.float64, device="cuda")
         mode = 1 if args.kernel == "gemm_mixed" else 0
         L = pkg.lib()

@@ -141,7 +141,7 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 // ------------------------------------------------------------- geometry
 constexpr int kTM = 128;        // rows per CTA (MMA M)
 constexpr int kKC = 32;         // K chunk per pipeline stage
-constexpr int kThreads = 128;   // one thread per row of the tile
+constexpr int kThreads = 256;   // two threads per row of the tile (each cuts half of a chunk)
 constexpr int kMaxT = 448;      // exactness bound of the FP64 form
 
 template <int S, int NT>
@@ -250,7 +250,7 @@ __global__ void prep_b_kernel(const double *__restrict__ Q, int64_t ldq, int t, 
 template <int S, int NT, bool OZAKI, typename WT>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k,
-               const uint16_t *__restrict__ Bs, const int *__restrict__ fexp, int nchunks,
+               const uint16_t *__restrict__ Bs, const int *__restrict__ fexp, int nchunks, int ncb,
                double *__restrict__ C, int64_t ldc, float *__restrict__ C32, int *err)
 {
     constexpr int G = OZAKI ? 10 : 1;           // accumulators
@@ -263,11 +263,16 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t mma_done[2];
     __shared__ uint32_t tmem_base_slot;
+    __shared__ int s_er[kTM];
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * kTM;
-    const int cb = blockIdx.y;
-    const int64_t r = row0 + tid;
+    const int trow = tid & (kTM - 1), half = tid >> 7;
+    // the column blocks of one row tile are adjacent in launch order, so the
+    // tile's rows of W are re-read from L2 rather than DRAM
+    const int64_t tile = (int64_t)blockIdx.x / ncb;
+    const int cb = (int)(blockIdx.x % ncb);
+    const int64_t row0 = tile * kTM;
+    const int64_t r = row0 + trow;
     const bool row_ok = r < rows;
 
     if (tid == 0) {
@@ -284,10 +289,18 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
     tc_fence_after();
     const uint32_t tmem = tmem_base_slot;
 
-    // row exponent (FP64 form)
+    // row exponent (FP64 form): each half scans half of the columns
     int e_r = -100000;
-    if (OZAKI && row_ok)
-        for (int c = 0; c < t; c++) e_r = max(e_r, dexp_of((double)W[r + (int64_t)c * ldw]));
+    if (OZAKI) {
+        int e_h = -100000;
+        if (row_ok)
+            for (int c = half; c < t; c += 2) e_h = max(e_h, dexp_of((double)W[r + (int64_t)c * ldw]));
+        if (half == 1) s_er[trow] = e_h;
+        __syncthreads();
+        if (half == 0) s_er[trow] = max(e_h, s_er[trow]);
+        __syncthreads();
+        e_r = s_er[trow];
+    }
 
     uint32_t parity[2] = {0u, 0u};
     bool used[2] = {false, false};
@@ -307,9 +320,10 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
             uint4 *dst = (uint4 *)B;
             for (int i = tid; i < Cfg::b_bytes / 16; i += kThreads) dst[i] = src[i];
         }
-        // A slices: this thread's row, 4 groups of 8 consecutive K entries
+        // A slices: this thread's row, its half of the 4 groups of 8 consecutive K entries
 #pragma unroll
-        for (int kg = 0; kg < kKC / 8; kg++) {
+        for (int kh = 0; kh < kKC / 16; kh++) {
+            const int kg = half * (kKC / 16) + kh;
             float pc[S][8];
 #pragma unroll
             for (int q = 0; q < 8; q++) {
@@ -327,7 +341,7 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
                     for (int s = 0; s < S; s++) pc[s][q] = p3[s];
                 }
             }
-            const int off = core_off(tid, kg * 8, kTM);
+            const int off = core_off(trow, kg * 8, kTM);
 #pragma unroll
             for (int s = 0; s < S; s++) {
                 uint4 w4;
@@ -380,10 +394,11 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
     } else {
-        // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows 32w..32w+31
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        // epilogue: warp w reads TMEM lanes 32(w mod 4).. = rows 32(w mod 4)..;
+        // the two halves take alternate groups of 8 columns
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const int j0 = cb * NT;
-        for (int c8 = 0; c8 < NT; c8 += 8) {
+        for (int c8 = half * 8; c8 < NT; c8 += 16) {
             if (j0 + c8 >= k) break;
             double out[8];
             if constexpr (OZAKI) {
@@ -471,9 +486,10 @@ static cudaError_t launch_tc(const WT *W, int64_t ldw, int64_t rows, int t, cons
     const int ncb = (k + NT - 1) / NT;
     dim3 pg((unsigned)((ncb * NT + 127) / 128), (unsigned)nchunks);
     prep_b_kernel<S, NT, OZAKI><<<pg, 128, 0, s>>>(Q, ldq, t, k, nchunks, ncb, bs, fexp);
-    dim3 grid((unsigned)((rows + kTM - 1) / kTM), (unsigned)ncb);
+    // 1-D grid over (row tile, column block), column block fastest
+    dim3 grid((unsigned)(((rows + kTM - 1) / kTM) * ncb));
     tc_gemm_kernel<S, NT, OZAKI, WT><<<grid, kThreads, Cfg::smem_bytes, s>>>(W, ldw, rows, t, k, bs, fexp,
-                                                                          nchunks, C, ldc, C32, err);
+                                                                          nchunks, ncb, C, ldc, C32, err);
     return cudaGetLastError();
 }
 

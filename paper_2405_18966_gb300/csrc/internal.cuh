@@ -52,7 +52,7 @@ struct Chunk {
 Chunk make_chunk(int64_t len, int target_blocks);
 
 // Row-length bins of a CSR matrix for the binned SpMV kernel.
-constexpr int kNumBins = 7;  // lanes per row: 1,2,4,8,16,32 and a whole CTA
+constexpr int kNumBins = 10;  // lanes per row: 1 (four length classes), 2, 4, 8, 16, 32, a whole CTA
 struct Bins {
     int64_t row_start[kNumBins + 1] = {0};    // offsets into perm
     int64_t block_start[kNumBins + 1] = {0};  // CTA offsets of each bin in the single launch
@@ -64,9 +64,22 @@ struct DevCSR {
     int32_t *col = nullptr;      // nnz
     double *val = nullptr;       // nnz (FP64 contexts)
     float *val32 = nullptr;      // nnz (MIXED contexts)
-    int32_t *perm = nullptr;     // m: rows grouped by bin, ascending inside a bin
+    // SELL-32 part (Kreutzer et al., SELL-C-sigma with C = 32 and full sorting):
+    // rows with at most kSellMaxLen entries, sorted by length (descending),
+    // cut into slices of 32 rows, each slice padded to its longest row and
+    // stored column-major, so one thread per row loads coalesced values.
+    int64_t sell_rows = 0;
+    int64_t sell_slices = 0;
+    int32_t *sell_perm = nullptr;    // original row of each SELL row
+    int64_t *sell_off = nullptr;     // element offset of each slice (sell_slices + 1)
+    int32_t *sell_col = nullptr;
+    double *sell_val = nullptr;
+    float *sell_val32 = nullptr;
+    // longer rows: grouped by row-length bin (warp / CTA per row)
+    int32_t *perm = nullptr;     // rows grouped by bin, ascending inside a bin
     Bins bins;
 };
+constexpr int kSellMaxLen = 128;
 
 struct DevDense {
     int64_t m = 0, n = 0, ld = 0;
@@ -74,7 +87,7 @@ struct DevDense {
 };
 
 constexpr int kSpmvThreads = 256;
-constexpr int kRowThreads = 256;
+constexpr int kRowThreads = 512;
 
 // ---- products (spmv.cu)
 // y = A x - coef * z (z may be null; coef from *coef_dev when non-null, else coef_h)

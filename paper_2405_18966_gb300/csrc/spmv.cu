@@ -65,10 +65,40 @@ csr_spmv_binned(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__
                 const int32_t *__restrict__ perm, const __grid_constant__ Bins bins,
                 const double *__restrict__ z,
                 const double *__restrict__ coef_dev, double coef_h, double *__restrict__ y,
-                const int *poison)
+                const int *poison, int64_t sell_rows, int64_t sell_blocks,
+                const int32_t *__restrict__ sell_perm, const int64_t *__restrict__ sell_off,
+                const int32_t *__restrict__ sell_col, const VT *__restrict__ sell_val)
 {
     if (poison && *(volatile const int *)poison) return;
-    const int64_t b = blockIdx.x;
+    if ((int64_t)blockIdx.x < sell_blocks) {
+        // SELL-32: one thread per row, slice-column-major storage
+        const int64_t i = (int64_t)blockIdx.x * kSpmvThreads + threadIdx.x;
+        if (i >= sell_rows) return;
+        const int64_t sl = i >> 5;
+        const int lane = (int)(i & 31);
+        const int64_t off = sell_off[sl];
+        const int w = (int)((sell_off[sl + 1] - off) >> 5);
+        const int32_t *cp = sell_col + off + lane;
+        const VT *vp = sell_val + off + lane;
+        AT a0 = AT(0), a1 = AT(0), a2 = AT(0), a3 = AT(0);
+        int j = 0;
+        for (; j + 3 < w; j += 4) {
+            const int32_t c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1)), c2 = __ldg(cp + 32 * (j + 2)),
+                          c3 = __ldg(cp + 32 * (j + 3));
+            const VT v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1)), v2 = __ldg(vp + 32 * (j + 2)),
+                     v3 = __ldg(vp + 32 * (j + 3));
+            a0 += AT(v0) * AT(__ldg(x + c0));
+            a1 += AT(v1) * AT(__ldg(x + c1));
+            a2 += AT(v2) * AT(__ldg(x + c2));
+            a3 += AT(v3) * AT(__ldg(x + c3));
+        }
+        for (; j < w; j++) a0 += AT(__ldg(vp + 32 * j)) * AT(__ldg(x + __ldg(cp + 32 * j)));
+        const int64_t r = sell_perm[i];
+        const double coef = coef_dev ? *coef_dev : coef_h;
+        y[r] = double((a0 + a1) + (a2 + a3)) - (z ? coef * z[r] : 0.0);
+        return;
+    }
+    const int64_t b = blockIdx.x - sell_blocks;
     int bin = 0;
 #pragma unroll
     for (int i = 1; i < kNumBins; i++)
@@ -77,12 +107,15 @@ csr_spmv_binned(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__
     const double coef = coef_dev ? *coef_dev : coef_h;
     const int64_t rb = bins.row_start[bin], re = bins.row_start[bin + 1];
     switch (bin) {
-    case 0: spmv_bin<1, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
-    case 1: spmv_bin<2, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
-    case 2: spmv_bin<4, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
-    case 3: spmv_bin<8, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
-    case 4: spmv_bin<16, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
-    case 5: spmv_bin<32, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
+    case 0:
+    case 1:
+    case 2:
+    case 3: spmv_bin<1, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
+    case 4: spmv_bin<2, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
+    case 5: spmv_bin<4, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
+    case 6: spmv_bin<8, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
+    case 7: spmv_bin<16, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
+    case 8: spmv_bin<32, VT, XT, AT>(row_ptr, col, val, x, perm, rb, re, lb, z, coef, y); return;
     default: break;
     }
     // a whole CTA per (very long) row
@@ -103,24 +136,29 @@ csr_spmv_binned(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__
 }
 
 static int64_t bin_blocks(const Bins &b) { return b.block_start[kNumBins]; }
+static int64_t sell_blocks(const DevCSR &A) { return (A.sell_rows + kSpmvThreads - 1) / kSpmvThreads; }
 
 cudaError_t csr_spmv_f64(const DevCSR &A, const double *x, const double *z, const double *coef_dev,
                          double coef_h, double *y, const int *poison, cudaStream_t s)
 {
-    const int64_t nblk = bin_blocks(A.bins);
+    const int64_t sb = sell_blocks(A);
+    const int64_t nblk = sb + bin_blocks(A.bins);
     if (nblk == 0) return cudaSuccess;
     csr_spmv_binned<double, double, double><<<(unsigned)nblk, kSpmvThreads, 0, s>>>(
-        A.row_ptr, A.col, A.val, x, A.perm, A.bins, z, coef_dev, coef_h, y, poison);
+        A.row_ptr, A.col, A.val, x, A.perm, A.bins, z, coef_dev, coef_h, y, poison, A.sell_rows, sb,
+        A.sell_perm, A.sell_off, A.sell_col, A.sell_val);
     return cudaGetLastError();
 }
 
 cudaError_t csr_spmv_f32(const DevCSR &A, const float *x, const double *z, const double *coef_dev,
                          double coef_h, double *y, const int *poison, cudaStream_t s)
 {
-    const int64_t nblk = bin_blocks(A.bins);
+    const int64_t sb = sell_blocks(A);
+    const int64_t nblk = sb + bin_blocks(A.bins);
     if (nblk == 0) return cudaSuccess;
     csr_spmv_binned<float, float, float><<<(unsigned)nblk, kSpmvThreads, 0, s>>>(
-        A.row_ptr, A.col, A.val32, x, A.perm, A.bins, z, coef_dev, coef_h, y, poison);
+        A.row_ptr, A.col, A.val32, x, A.perm, A.bins, z, coef_dev, coef_h, y, poison, A.sell_rows, sb,
+        A.sell_perm, A.sell_off, A.sell_col, A.sell_val32);
     return cudaGetLastError();
 }
 
@@ -494,40 +532,133 @@ __global__ void transpose_fill(const int64_t *__restrict__ keys, int64_t nnz,
 // Lanes per row are chosen so that each lane does >= 4 FMAs: on GB300 every
 // warp-wide FP64 instruction occupies the FP64 pipe for 16 SM cycles, so a
 // shuffle reduction over many lanes of a short row costs more than its FMAs.
+// Lanes per row are chosen so that each lane does >= 4 FMAs: on GB300 every
+// warp-wide FP64 instruction occupies the FP64 pipe for 16 SM cycles, so a
+// shuffle reduction over many lanes of a short row costs more than its FMAs.
+// Rows handled by one lane are further split by length (1, 2, 3-4, 5-8) so
+// the lanes of a warp run loops of similar length.
 static int bin_of(int64_t len)
 {
-    if (len <= 8) return 0;      // 1 lane per row
-    if (len <= 16) return 1;     // 2
-    if (len <= 32) return 2;     // 4
-    if (len <= 64) return 3;     // 8
-    if (len <= 128) return 4;    // 16
-    if (len <= 4096) return 5;   // 32 (a warp)
-    return 6;                    // a CTA
+    if (len <= 1) return 0;      // 1 lane per row
+    if (len <= 2) return 1;
+    if (len <= 4) return 2;
+    if (len <= 8) return 3;
+    if (len <= 16) return 4;     // 2
+    if (len <= 32) return 5;     // 4
+    if (len <= 64) return 6;     // 8
+    if (len <= 128) return 7;    // 16
+    if (len <= 4096) return 8;   // 32 (a warp)
+    return 9;                    // a CTA
 }
 
-// Groups rows by bin (ascending row order inside a bin) and uploads perm.
+static int bin_lanes(int bin) { return bin <= 3 ? 1 : (bin == 9 ? kSpmvThreads : 1 << (bin - 3)); }
+
+// Fills the padded SELL-32 arrays: thread per (slice, lane); lanes past the
+// last row of the last slice are all padding.
+__global__ void sell_fill_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                 const double *__restrict__ val, const float *__restrict__ val32,
+                                 const int32_t *__restrict__ sell_perm, const int64_t *__restrict__ sell_off,
+                                 int64_t sell_rows, int64_t slices, int32_t *__restrict__ scol,
+                                 double *__restrict__ sval, float *__restrict__ sval32)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= slices * 32) return;
+    const int64_t sl = i >> 5;
+    const int lane = (int)(i & 31);
+    const int64_t off = sell_off[sl];
+    const int w = (int)((sell_off[sl + 1] - off) >> 5);
+    int64_t e0 = 0, len = 0;
+    if (i < sell_rows) {
+        const int64_t r = sell_perm[i];
+        e0 = row_ptr[r];
+        len = row_ptr[r + 1] - e0;
+    }
+    for (int j = 0; j < w; j++) {
+        const int64_t d = off + (int64_t)j * 32 + lane;
+        const bool real = j < len;
+        scol[d] = real ? col[e0 + j] : 0;
+        if (sval) sval[d] = real ? val[e0 + j] : 0.0;
+        if (sval32) sval32[d] = real ? val32[e0 + j] : 0.f;
+    }
+}
+
+// Rows with <= kSellMaxLen entries go to the SELL-32 part (sorted by length,
+// descending, then by row); longer rows are grouped by bin (ascending row
+// order inside a bin).  Uploads both layouts.
 static int build_bins(DevCSR *A, const std::vector<int64_t> &rp, cudaStream_t s)
 {
     const int64_t m = A->m;
+    // SELL part: counting sort by length, descending
+    std::vector<int64_t> lcnt(kSellMaxLen + 2, 0);
+    for (int64_t r = 0; r < m; r++) {
+        const int64_t L = rp[r + 1] - rp[r];
+        if (L <= kSellMaxLen) lcnt[L]++;
+    }
+    std::vector<int64_t> lpos(kSellMaxLen + 2, 0);
+    int64_t acc = 0;
+    for (int L = kSellMaxLen; L >= 0; L--) { lpos[L] = acc; acc += lcnt[L]; }
+    const int64_t sr = acc;
+    std::vector<int32_t> sperm((size_t)std::max<int64_t>(sr, 1));
+    for (int64_t r = 0; r < m; r++) {
+        const int64_t L = rp[r + 1] - rp[r];
+        if (L <= kSellMaxLen) sperm[lpos[L]++] = (int32_t)r;
+    }
+    const int64_t slices = (sr + 31) / 32;
+    std::vector<int64_t> soff((size_t)slices + 1, 0);
+    for (int64_t sl = 0; sl < slices; sl++) {
+        const int32_t r = sperm[sl * 32];  // the longest row of the slice comes first
+        soff[sl + 1] = soff[sl] + 32 * (rp[r + 1] - rp[r]);
+    }
+    A->sell_rows = sr;
+    A->sell_slices = slices;
+    const int64_t padded = soff[(size_t)slices];
+    if (cudaMalloc(&A->sell_perm, sizeof(int32_t) * (size_t)std::max<int64_t>(sr, 1)) != cudaSuccess ||
+        cudaMalloc(&A->sell_off, sizeof(int64_t) * (size_t)(slices + 1)) != cudaSuccess ||
+        cudaMalloc(&A->sell_col, sizeof(int32_t) * (size_t)std::max<int64_t>(padded, 1)) != cudaSuccess)
+        return SVDSC_ERR_NOMEM;
+    if (A->val && cudaMalloc(&A->sell_val, sizeof(double) * (size_t)std::max<int64_t>(padded, 1)) != cudaSuccess)
+        return SVDSC_ERR_NOMEM;
+    if (A->val32 && cudaMalloc(&A->sell_val32, sizeof(float) * (size_t)std::max<int64_t>(padded, 1)) != cudaSuccess)
+        return SVDSC_ERR_NOMEM;
+    if (sr > 0 && cudaMemcpyAsync(A->sell_perm, sperm.data(), sizeof(int32_t) * (size_t)sr, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        return SVDSC_ERR_CUDA;
+    if (cudaMemcpyAsync(A->sell_off, soff.data(), sizeof(int64_t) * (size_t)(slices + 1), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return SVDSC_ERR_CUDA;
+    if (slices > 0)
+        sell_fill_kernel<<<(unsigned)((slices * 32 + 255) / 256), 256, 0, s>>>(
+            A->row_ptr, A->col, A->val, A->val32, A->sell_perm, A->sell_off, sr, slices, A->sell_col, A->sell_val,
+            A->sell_val32);
+    if (cudaGetLastError() != cudaSuccess) return SVDSC_ERR_CUDA;
+
+    // binned part (rows longer than kSellMaxLen)
     std::vector<int64_t> cnt(kNumBins, 0);
-    for (int64_t r = 0; r < m; r++) cnt[bin_of(rp[r + 1] - rp[r])]++;
+    int64_t nlong = 0;
+    for (int64_t r = 0; r < m; r++) {
+        const int64_t L = rp[r + 1] - rp[r];
+        if (L > kSellMaxLen) { cnt[bin_of(L)]++; nlong++; }
+    }
     Bins b;
     b.row_start[0] = 0;
     for (int i = 0; i < kNumBins; i++) b.row_start[i + 1] = b.row_start[i] + cnt[i];
     b.block_start[0] = 0;
     for (int i = 0; i < kNumBins; i++) {
-        const int64_t rows_per_block = (i < 6) ? (kSpmvThreads >> i) : 1;
+        const int64_t rows_per_block = kSpmvThreads / bin_lanes(i);
         b.block_start[i + 1] = b.block_start[i] + (cnt[i] + rows_per_block - 1) / rows_per_block;
     }
-    if (b.block_start[kNumBins] > 0x7fffffff) return SVDSC_ERR_SIZE;
-    std::vector<int32_t> perm((size_t)std::max<int64_t>(m, 1));
+    if (b.block_start[kNumBins] + (sr + kSpmvThreads - 1) / kSpmvThreads > 0x7fffffff) return SVDSC_ERR_SIZE;
+    std::vector<int32_t> perm((size_t)std::max<int64_t>(nlong, 1));
     std::vector<int64_t> pos(b.row_start, b.row_start + kNumBins);
-    for (int64_t r = 0; r < m; r++) perm[pos[bin_of(rp[r + 1] - rp[r])]++] = (int32_t)r;
+    for (int64_t r = 0; r < m; r++) {
+        const int64_t L = rp[r + 1] - rp[r];
+        if (L > kSellMaxLen) perm[pos[bin_of(L)]++] = (int32_t)r;
+    }
     A->bins = b;
-    if (cudaMalloc(&A->perm, sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1)) != cudaSuccess)
+    if (cudaMalloc(&A->perm, sizeof(int32_t) * (size_t)std::max<int64_t>(nlong, 1)) != cudaSuccess)
         return SVDSC_ERR_NOMEM;
-    if (cudaMemcpyAsync(A->perm, perm.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
+    if (nlong > 0 && cudaMemcpyAsync(A->perm, perm.data(), sizeof(int32_t) * (size_t)nlong, cudaMemcpyHostToDevice,
+                                     s) != cudaSuccess)
         return SVDSC_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SVDSC_ERR_CUDA;
     return SVDSC_OK;
@@ -535,6 +666,11 @@ static int build_bins(DevCSR *A, const std::vector<int64_t> &rp, cudaStream_t s)
 
 void csr_free(DevCSR *A)
 {
+    cudaFree(A->sell_perm);
+    cudaFree(A->sell_off);
+    cudaFree(A->sell_col);
+    cudaFree(A->sell_val);
+    cudaFree(A->sell_val32);
     cudaFree(A->row_ptr);
     cudaFree(A->col);
     cudaFree(A->val);
