@@ -305,7 +305,7 @@ def run_batch(args, ws, rank):
     mats = [it.a for it in items]
     ks = [it.k for it in items]
     t0 = time.perf_counter()
-    b = pkg.Batch(mats, ks, ks, seed=1)
+    b = pkg.Batch(mats, ks, ks, seed=1, cluster=args.batch_cluster)
     create_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         out = b.solve(1e-10, 1000, out="device")
@@ -319,6 +319,18 @@ def run_batch(args, ws, rank):
     clocks = sampler.stop()
     infos = out["infos"]
     nconv = sum(i["converged"] for i in infos)
+    prof = b.profile()
+    clk = 2.07e9 if clocks is None else clocks["sm_mhz"] * 1e6
+    per_cluster = {}
+    for c, cyc in zip(prof["cluster"], prof["cycles_total"]):
+        per_cluster[int(c)] = per_cluster.get(int(c), 0) + int(cyc)
+    loads = np.array(sorted(per_cluster.values())) / clk
+    rs = np.array([i["restarts"] for i in infos])
+    balance = {"cluster_busy_s_max": float(loads.max()), "cluster_busy_s_mean": float(loads.mean()),
+               "svd_share": float(prof["cycles_svd"].sum() / max(1, prof["cycles_total"].sum())),
+               "lbp_share": float(prof["cycles_lbp"].sum() / max(1, prof["cycles_total"].sum())),
+               "restarts_max": int(rs.max()), "restarts_p90": float(np.percentile(rs, 90)),
+               "slowest_matrix_s": float(prof["cycles_total"].max() / clk)}
     tot_bytes = sum(batch_bytes(inf, it.a.m, it.a.n, it.a.nnz, it.k) for inf, it in zip(infos, items))
     launches = 1 * args.steps
     # plain GPU form (one svdsc_solve per matrix, FP64) on a sample, and the sigma error of the batch vs it
@@ -349,7 +361,8 @@ def run_batch(args, ws, rank):
            "batch": {"converged": nconv, "restarts_mean": float(np.mean([i["restarts"] for i in infos])),
                      "create_s": create_s, "generate_s": gen_s, "tuning": b.tuning(0), "layout": b.layout(),
                      "plain_fp64_gpu_s_estimate": plain_est, "speedup_vs_plain_gpu": plain_est / wall,
-                     "sigma_rel_err_vs_plain_fp64_max": max(errs), "plain_sample": len(sample)},
+                     "sigma_rel_err_vs_plain_fp64_max": max(errs), "plain_sample": len(sample),
+                     "balance": balance},
            "hbm": {"alg_gbs": gbs, "frac_of_measured": gbs / peaks["hbm_gbs"]},
            "gpu_launches": launches, "clocks": clocks, "cpu_baseline": None, "e2e": None}
     print(json.dumps(res), flush=True)
@@ -432,6 +445,7 @@ def main():
     ap.add_argument("--ncols", type=int, default=150, help="basis columns for --kernel cgs2 / gemm t")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch-frac", type=float, default=1.0, help="fraction of the 256-matrix batch")
+    ap.add_argument("--batch-cluster", type=int, default=0, help="CTAs per matrix (0: automatic)")
     args = ap.parse_args()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -291,9 +291,16 @@ int svdsc_batch_tuning(const svdsc_batch *b, int i, int *lanes_A, int *lanes_AT,
 /* CTAs per matrix (thread-block cluster size: the rows of A, A^T and of the
  * bases are split across them) and the number of clusters of the persistent
  * launch.  Automatic choice: the smallest power of two <= 8 for which the
- * costliest matrix, run on one cluster, takes at most twice its share of the
+ * costliest matrix, run on one cluster, takes at most its share of the
  * batch's estimated work. */
 int svdsc_batch_layout(const svdsc_batch *b, int *cluster_size, int *clusters);
+
+/* Per-matrix profile of the last batch solve (arrays of nb entries, each may
+ * be NULL): SM clock cycles of the whole solve, of the projected SVDs and of
+ * the Lanczos segments on the cluster's first CTA, and the cluster that
+ * solved the matrix. */
+int svdsc_batch_profile(const svdsc_batch *b, int64_t *cycles_total, int64_t *cycles_svd,
+                        int64_t *cycles_lbp, int32_t *cluster);
 
 int svdsc_batch_destroy(svdsc_batch *b);
 

@@ -33,7 +33,7 @@ F64, F32 = 0, 1
 EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "svdsc_matvec",
            "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc",
            "svdsc_gemm", "svdsc_batch_create", "svdsc_batch_solve", "svdsc_batch_tuning",
-           "svdsc_batch_destroy", "svdsc_solve_batched", "svdsc_batch_layout")
+           "svdsc_batch_destroy", "svdsc_solve_batched", "svdsc_batch_layout", "svdsc_batch_profile")
 
 
 class SvdscMatrix(C.Structure):
@@ -100,6 +100,7 @@ def lib():
                                          C.POINTER(dbl)]
         L.svdsc_batch_destroy.argtypes = [vp]
         L.svdsc_batch_layout.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+        L.svdsc_batch_profile.argtypes = [vp, vp, vp, vp, vp]
         L.svdsc_solve_batched.argtypes = [i32, C.POINTER(SvdscMatrix), vp, vp, dbl, i32, vp, vp, vp, vp,
                                           i32, C.POINTER(SvdscOptions), C.POINTER(SvdscInfo)]
         for name in EXPORTS:
@@ -324,6 +325,14 @@ class Batch:
         a, b = C.c_int(), C.c_int()
         _check(lib().svdsc_batch_layout(self.handle, C.byref(a), C.byref(b)), "svdsc_batch_layout")
         return {"cluster_size": a.value, "clusters": b.value}
+
+    def profile(self):
+        nb = len(self.shapes)
+        tot, svd, lbp = (np.zeros(nb, dtype=np.int64) for _ in range(3))
+        cl = np.zeros(nb, dtype=np.int32)
+        _check(lib().svdsc_batch_profile(self.handle, _ptr(tot), _ptr(svd), _ptr(lbp), _ptr(cl)),
+               "svdsc_batch_profile")
+        return {"cycles_total": tot, "cycles_svd": svd, "cycles_lbp": lbp, "cluster": cl}
 
     def tuning(self, i):
         a, b, c, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()

@@ -51,6 +51,8 @@ struct BStat {
     int64_t n_matvec, n_steps;
     double anorm, beta_t;
     int err, svd_sweeps;
+    int64_t cycles_total, cycles_svd, cycles_lbp;  // SM clock cycles on the cluster leader
+    int cluster, pad;
 };
 
 struct BSlot {   // one per cluster (bases), T one per CTA
@@ -653,9 +655,12 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
     R.failed = false;
     double *red = sm + kSmRed;
     const int t = R.t, k = R.k;
+    const long long c_start = clock64();
+    long long c_svd = 0, c_lbp = 0;
     if (threadIdx.x == 0 && R.lead) {
         st->converged = 0; st->nconv = 0; st->restarts = 0; st->breakdowns = 0;
         st->n_matvec = 0; st->n_steps = 0; st->err = 0; st->svd_sweeps = 0;
+        st->cluster = (int)cl_id();
     }
     for (int64_t i = threadIdx.x; i < (int64_t)(t + 1) * (t + 1); i += kBT) R.T[i] = 0.0;
     // v_1: draw 0, normalised
@@ -675,10 +680,18 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
         if (threadIdx.x == 0 && R.lead) { st->n_matvec++; st->n_steps++; }
         __syncthreads();
     }
-    lbp_from(R, 1);
+    {
+        const long long c0 = clock64();
+        lbp_from(R, 1);
+        c_lbp += clock64() - c0;
+    }
     int restarts = 0;
     for (int it = 1; it <= P.maxit && !R.failed; it++) {
-        cta_small_svd(R);
+        {
+            const long long c0 = clock64();
+            cta_small_svd(R);
+            c_svd += clock64() - c0;
+        }
         const double *S = sm + kSmS, *ut = sm + kSmUt;
         double *rho = sm + kSmRho;
         const double beta_t = *Tb(R, t - 1, t);
@@ -731,7 +744,9 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
         __syncthreads();
         restarts++;
         if (threadIdx.x == 0 && R.lead) st->restarts = restarts;
+        const long long c0 = clock64();
         lbp_from(R, k + 1);
+        c_lbp += clock64() - c0;
     }
     if (!R.failed) {
         // outputs: S, this CTA's rows of U = U(:,1:t) Uh(:,1:k), V = V(:,1:t) Vh(:,1:k), sign rule
@@ -741,6 +756,11 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
         cta_gemm32(R.V32 + R.n0, R.ldv, R.n1 - R.n0, t, smf + kSmQV, k, M.V + R.n0, nullptr, R.n);
         cl_sign(R, M.U, R.m, M.V, R.n);
         if (threadIdx.x == 0 && R.lead) st->anorm = R.anorm;
+    }
+    if (threadIdx.x == 0 && R.lead) {
+        st->cycles_total = clock64() - c_start;
+        st->cycles_svd = c_svd;
+        st->cycles_lbp = c_lbp;
     }
     phase = R.phase;
 }
@@ -982,7 +1002,9 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     }
     if (rc) { svdsc_batch_destroy(B); return rc; }
     // cluster size: the smallest power of two (<= 8) for which the costliest
-    // matrix on its cluster is not the bottleneck of the whole batch
+    // matrix on its cluster takes at most its share of the batch's estimated
+    // work (restart counts are not known in advance and vary widely, so the
+    // rule leans towards larger clusters)
     auto est_cost = [&](int b) {
         const BMat &M = B->hm[b];
         return (double)(M.m + M.n) * M.t * M.t + 4.0 * (double)M.nnz * M.t;
@@ -990,7 +1012,7 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     double total = 0.0, worst = 0.0;
     for (int b = 0; b < nb; b++) { total += est_cost(b); worst = std::max(worst, est_cost(b)); }
     int C = 1;
-    while (C < 8 && worst * nsm > 2.0 * total * C) C *= 2;
+    while (C < 8 && worst * nsm > total * C) C *= 2;
     if (opt && opt->batch_cluster > 0) C = opt->batch_cluster;  // explicit: 1, 2, 4 or 8
     if (C != 1 && C != 2 && C != 4 && C != 8) { svdsc_batch_destroy(B); return SVDSC_ERR_ARG; }
     B->csize = C;
@@ -1183,6 +1205,22 @@ int svdsc_batch_tuning(const svdsc_batch *B, int b, int *lanes_A, int *lanes_AT,
     if (lanes_AT) *lanes_AT = B->hm[b].gAT;
     if (gemv_cols) *gemv_cols = B->hm[b].tc;
     if (tune_ms) *tune_ms = B->tune_ms;
+    return SVDSC_OK;
+}
+
+int svdsc_batch_profile(const svdsc_batch *B, int64_t *cycles_total, int64_t *cycles_svd, int64_t *cycles_lbp,
+                        int32_t *cluster)
+{
+    if (!B) return SVDSC_ERR_ARG;
+    std::vector<BStat> st(B->nb);
+    if (cudaMemcpy(st.data(), B->d_stats, sizeof(BStat) * B->nb, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SVDSC_ERR_CUDA;
+    for (int b = 0; b < B->nb; b++) {
+        if (cycles_total) cycles_total[b] = st[b].cycles_total;
+        if (cycles_svd) cycles_svd[b] = st[b].cycles_svd;
+        if (cycles_lbp) cycles_lbp[b] = st[b].cycles_lbp;
+        if (cluster) cluster[b] = st[b].cluster;
+    }
     return SVDSC_OK;
 }
 
