@@ -446,6 +446,9 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch-frac", type=float, default=1.0, help="fraction of the 256-matrix batch")
     ap.add_argument("--batch-cluster", type=int, default=0, help="CTAs per matrix (0: automatic)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
+                    help="override the workload's precision (mixed: values rounded to FP32; the FP64 solve "
+                         "of the same rounded matrix is run once, untimed, for the sigma error)")
     args = ap.parse_args()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -464,6 +467,26 @@ def main():
 
     peaks, peak_src = load_peaks()
     A, k, p, tol, prec = make_workload(args.workload, args.scale)
+    ref_fp64 = None
+    if args.precision and args.precision != prec and hasattr(A, "row_ptr"):
+        prec = args.precision
+        if prec == "mixed":
+            A.values = A.values.astype(np.float32)
+            A64 = synth.CSR(A.m, A.n, A.row_ptr, A.col_idx, A.values.astype(np.float64))
+            v0r = synth.start_vector(A.n, 1)
+            with pkg.Solver(A64) as s64:
+                v0d = torch.tensor(v0r, device="cuda")
+                o64 = (torch.empty(k, dtype=torch.float64, device="cuda"),
+                       torch.empty((k, A.m), dtype=torch.float64, device="cuda"),
+                       torch.empty((k, A.n), dtype=torch.float64, device="cuda"),
+                       torch.empty(k, dtype=torch.float64, device="cuda"))
+                s64.solve(k, p, tol, 1000, v0=v0d, outputs=o64)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ref_fp64 = s64.solve(k, p, tol, 1000, v0=v0d, outputs=o64)
+                torch.cuda.synchronize()
+                ref_fp64_s = time.perf_counter() - t0
+                ref_fp64.S = ref_fp64.S.cpu().numpy()
     v0 = synth.start_vector(A.n, 1)
     cfg = describe(A, args.workload, k, p, tol, prec)
     cfg["l2"] = "inputs larger than L2 (no flush): A, A^T and the Lanczos bases exceed 129 MB" \
@@ -570,6 +593,12 @@ def main():
                           f"SVD; extrapolated by algorithmic bytes / GEMM rows / SVD count to the solve the "
                           f"GPU ran ({info['restarts']} restarts)")}
 
+    mixed_vs_fp64 = None
+    if ref_fp64 is not None:
+        Sm = r.S.cpu().numpy() if hasattr(r.S, "cpu") else np.asarray(r.S)
+        mixed_vs_fp64 = {"fp64_gpu_s": ref_fp64_s, "speedup": ref_fp64_s / (ms / 1e3),
+                         "sigma_rel_err_max": float(np.max(np.abs(Sm - ref_fp64.S) / ref_fp64.S)),
+                         "fp64_restarts": ref_fp64.info["restarts"]}
     out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
@@ -578,7 +607,8 @@ def main():
            "solve": {"restarts": info["restarts"], "converged": info["converged"], "nconv": info["nconv"],
                      "n_matvec": info["n_matvec"], "breakdowns": info["breakdowns"], "t": info["t"],
                      "phase_ms_per_step": phases_ms, "anorm_est": info["anorm_est"],
-                     "sigma_1": float(r.S[0]), "sigma_k": float(r.S[k - 1])}}
+                     "sigma_1": float(r.S[0]), "sigma_k": float(r.S[k - 1])},
+           "mixed_vs_fp64": mixed_vs_fp64}
     if rank == 0:
         print(json.dumps(out), flush=True)
     solver.close()

@@ -58,6 +58,7 @@ struct BStat {
 struct BSlot {   // one per cluster (bases), T one per CTA
     double *U0, *U1, *V0, *V1;
     float *U32_0, *U32_1, *V32_0, *V32_1;
+    float *wf;      // FP32 copy of the vector being orthogonalized (each CTA its rows)
     int64_t ldu, ldv;
 };
 
@@ -198,7 +199,7 @@ __device__ void cta_spmv(int G, const int64_t *rp, const int32_t *col, const flo
 // lane keeps 4 rows x (TC + 1) independent loads in flight (one SM works on
 // the whole matrix, so memory-level parallelism sets its bandwidth).
 template <typename WT, int TC>
-__device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, const double *__restrict__ w,
+__device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, const WT *__restrict__ w,
                            int64_t len, double *h)
 {
     using AT = WT;  // FP32 products and sums for the FP32 shadow, FP64 otherwise
@@ -240,8 +241,10 @@ __device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, cons
     __syncthreads();
 }
 
+// w has the type of W: the FP32 pass reads an FP32 copy of the vector
+// (double -> float conversions run on the FP64 pipe)
 template <typename WT>
-__device__ void cta_proj(int tc, const WT *W, int64_t ld, int ncols, const double *w, int64_t len, double *h)
+__device__ void cta_proj(int tc, const WT *W, int64_t ld, int ncols, const WT *w, int64_t len, double *h)
 {
     if (tc >= 4) cta_proj_t<WT, 4>(W, ld, ncols, w, len, h);
     else if (tc == 2) cta_proj_t<WT, 2>(W, ld, ncols, w, len, h);
@@ -300,20 +303,6 @@ __device__ double cta_norm2(const double *w, int64_t len, double *red)
     return cta_sum(nrm, red);
 }
 
-// CGS2 against ncols columns: pass 1 on the FP32 shadow, pass 2 in FP64.
-// Returns ||w||^2 after the second pass.
-__device__ double cta_cgs2(int tc, const double *W, const float *W32, int64_t ld, int ncols, double *w,
-                           int64_t len, double *h, float *h32, double *red)
-{
-    if (ncols <= 0) return cta_norm2(w, len, red);
-    cta_proj<float>(tc, W32, ld, ncols, w, len, h);
-    for (int c = threadIdx.x; c < ncols; c += kBT) h32[c] = (float)h[c];
-    __syncthreads();
-    cta_update<float, float>(W32, ld, ncols, h32, w, len, false, red);
-    cta_proj<double>(tc, W, ld, ncols, w, len, h);
-    return cta_update<double, double>(W, ld, ncols, h, w, len, true, red);
-}
-
 __device__ void cta_scale(double *w, float *w32, int64_t len, double inv)
 {
     for (int64_t r = threadIdx.x; r < len; r += kBT) {
@@ -325,6 +314,7 @@ __device__ void cta_scale(double *w, float *w32, int64_t len, double inv)
 }
 
 struct BRun {
+    float *wf;
     const BMat *M;
     BStat *st;
     double *U, *V, *Ua, *Va, *T;
@@ -384,7 +374,9 @@ __device__ double cl_cgs2(BRun &R, const double *W, const float *W32, int64_t ld
     float *h32 = R.smf + kSmH32;
     const int64_t len = r1 - r0;
     if (ncols <= 0) return cl_sum_scalar(R, cta_norm2(w + r0, len, red));
-    cta_proj<float>(R.tc, W32 + r0, ld, ncols, w + r0, len, part_buf(R));
+    for (int64_t j = threadIdx.x; j < len; j += kBT) R.wf[r0 + j] = (float)w[r0 + j];
+    __syncthreads();
+    cta_proj<float>(R.tc, W32 + r0, ld, ncols, R.wf + r0, len, part_buf(R));
     cl_gather(R, ncols, h);
     for (int c = threadIdx.x; c < ncols; c += kBT) h32[c] = (float)h[c];
     __syncthreads();
@@ -637,6 +629,7 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
 {
     BRun R;
     R.M = &M;
+    R.wf = slot.wf;
     R.st = st;
     R.U = slot.U0; R.Ua = slot.U1; R.V = slot.V0; R.Va = slot.V1; R.T = Tpriv;
     R.U32 = slot.U32_0; R.U32a = slot.U32_1; R.V32 = slot.V32_0; R.V32a = slot.V32_1;
@@ -1038,7 +1031,7 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     const int64_t ldu = (mmax + 63) & ~int64_t(63), ldv = (nmax + 63) & ~int64_t(63);
     const int64_t cols = tmax + 2;
     const size_t per_slot = sizeof(double) * (size_t)(2 * ldu * cols + 2 * ldv * cols + 64) +
-                            sizeof(float) * (size_t)(2 * ldu * cols + 2 * ldv * cols) + 4096;
+                            sizeof(float) * (size_t)(2 * ldu * cols + 2 * ldv * cols + std::max(ldu, ldv)) + 4096;
     std::vector<BSlot> slots(B->nslots);
     if (cudaMalloc(&B->slot_mem, per_slot * B->nslots) != cudaSuccess) { svdsc_batch_destroy(B); return SVDSC_ERR_NOMEM; }
     cudaMemsetAsync(B->slot_mem, 0, per_slot * B->nslots, B->stream);
@@ -1060,6 +1053,7 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
         S.U32_1 = (float *)take(sizeof(float) * ldu * cols);
         S.V32_0 = (float *)take(sizeof(float) * ldv * cols);
         S.V32_1 = (float *)take(sizeof(float) * ldv * cols);
+        S.wf = (float *)take(sizeof(float) * std::max(ldu, ldv));
     }
     // work order: largest estimated cost first
     std::vector<int> order(nb);

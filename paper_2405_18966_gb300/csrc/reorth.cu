@@ -40,9 +40,15 @@ proj_partial_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const doubl
 {
     if (poisoned(poison)) return;
     extern __shared__ double ws[];
+    // FP32 pass: the chunk of w is converted once (double -> float conversions
+    // run on the FP64 pipe, so none may sit in the inner loop)
+    float *ws32 = (float *)ws;
     const int64_t r0 = (int64_t)blockIdx.x * R;
     const int rows = (int)min(R, len - r0);
-    for (int j = threadIdx.x; j < rows; j += blockDim.x) ws[j] = w[r0 + j];
+    for (int j = threadIdx.x; j < rows; j += blockDim.x) {
+        if constexpr (sizeof(WT) == 8) ws[j] = w[r0 + j];
+        else ws32[j] = (float)w[r0 + j];
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c = warp; c < ncols; c += kProjWarps) {
@@ -65,20 +71,36 @@ proj_partial_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const doubl
             }
             s = (a0 + a1) + (a2 + a3);
         } else {
-            // FP32 shadow (first CGS pass of the mixed form): FP32 products and sums
+            // FP32 shadow (first CGS pass of the mixed form): FP32 products and
+            // sums, four 16-byte loads in flight per lane
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
             int j = 4 * lane;
+            for (; j + 387 < rows; j += 512) {
+                float4 v[4], x[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) v[u] = __ldcs((const float4 *)(col + j + 128 * u));
+#pragma unroll
+                for (int u = 0; u < 4; u++) x[u] = *(const float4 *)(ws32 + j + 128 * u);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    a0 = fmaf(v[u].x, x[u].x, a0);
+                    a1 = fmaf(v[u].y, x[u].y, a1);
+                    a2 = fmaf(v[u].z, x[u].z, a2);
+                    a3 = fmaf(v[u].w, x[u].w, a3);
+                }
+            }
             for (; j + 3 < rows; j += 128) {
                 const float4 v = __ldcs((const float4 *)(col + j));
-                a0 = fmaf(v.x, (float)ws[j], a0);
-                a1 = fmaf(v.y, (float)ws[j + 1], a1);
-                a2 = fmaf(v.z, (float)ws[j + 2], a2);
-                a3 = fmaf(v.w, (float)ws[j + 3], a3);
+                const float4 x = *(const float4 *)(ws32 + j);
+                a0 = fmaf(v.x, x.x, a0);
+                a1 = fmaf(v.y, x.y, a1);
+                a2 = fmaf(v.z, x.z, a2);
+                a3 = fmaf(v.w, x.w, a3);
             }
             // this lane's last, partial group of four
 #pragma unroll
             for (int q = 0; q < 4; q++)
-                if (j + q < rows) a0 = fmaf((float)col[j + q], (float)ws[j + q], a0);
+                if (j + q < rows) a0 = fmaf((float)col[j + q], ws32[j + q], a0);
             s = (double)((a0 + a1) + (a2 + a3));
         }
 #pragma unroll
@@ -150,7 +172,11 @@ update_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__r
     if (poisoned(poison)) return;
     extern __shared__ double hs[];
     __shared__ double red[kRowThreads / 32];
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = h[c];
+    float *hs32 = (float *)(hs + ncols);  // FP32 copy for the FP32 pass (converted once)
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+        hs[c] = h[c];
+        if constexpr (sizeof(WT) == 4) hs32[c] = (float)h[c];
+    }
     __syncthreads();
     const int64_t r0 = (int64_t)blockIdx.x * R;
     const int rows = (int)min(R, len - r0);
@@ -180,15 +206,15 @@ update_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__r
                 for (; c + 1 < ncols; c += 2) {
                     const float2 v0 = __ldcs((const float2 *)(p + (int64_t)c * ld));
                     const float2 v1 = __ldcs((const float2 *)(p + (int64_t)(c + 1) * ld));
-                    f0 = fmaf(v0.x, (float)hs[c], f0);
-                    f1 = fmaf(v0.y, (float)hs[c], f1);
-                    g0 = fmaf(v1.x, (float)hs[c + 1], g0);
-                    g1 = fmaf(v1.y, (float)hs[c + 1], g1);
+                    f0 = fmaf(v0.x, hs32[c], f0);
+                    f1 = fmaf(v0.y, hs32[c], f1);
+                    g0 = fmaf(v1.x, hs32[c + 1], g0);
+                    g1 = fmaf(v1.y, hs32[c + 1], g1);
                 }
                 for (; c < ncols; c++) {
                     const float2 v0 = __ldcs((const float2 *)(p + (int64_t)c * ld));
-                    f0 = fmaf(v0.x, (float)hs[c], f0);
-                    f1 = fmaf(v0.y, (float)hs[c], f1);
+                    f0 = fmaf(v0.x, hs32[c], f0);
+                    f1 = fmaf(v0.y, hs32[c], f1);
                 }
                 a0 = (double)f0; a1 = (double)f1; b0 = (double)g0; b1 = (double)g1;
             }
@@ -200,7 +226,13 @@ update_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__r
             nrm = fma(n1, n1, nrm);
         } else {
             double a0 = 0.0;
-            for (int c = 0; c < ncols; c++) a0 = fma((double)W[r + (int64_t)c * ld], hs[c], a0);
+            if constexpr (sizeof(WT) == 4) {
+                float f = 0.f;
+                for (int c = 0; c < ncols; c++) f = fmaf((float)W[r + (int64_t)c * ld], hs32[c], f);
+                a0 = (double)f;
+            } else {
+                for (int c = 0; c < ncols; c++) a0 = fma((double)W[r + (int64_t)c * ld], hs[c], a0);
+            }
             const double n0 = w[r] - a0;
             w[r] = n0;
             nrm = fma(n0, n0, nrm);
@@ -224,8 +256,8 @@ void update_sub_f32(const float *W32, int64_t ld, int ncols, const double *h, do
                     const Chunk &c, const int *poison, cudaStream_t s)
 {
     if (ncols <= 0) return;
-    update_kernel<float><<<c.nb, kRowThreads, sizeof(double) * ncols, s>>>(W32, ld, ncols, h, w, c.len,
-                                                                          c.R, nullptr, poison);
+    update_kernel<float><<<c.nb, kRowThreads, sizeof(double) * ncols + sizeof(float) * ncols, s>>>(
+        W32, ld, ncols, h, w, c.len, c.R, nullptr, poison);
 }
 
 __global__ void __launch_bounds__(kRowThreads)
