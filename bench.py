@@ -330,7 +330,12 @@ def run_batch(args, ws, rank):
                "svd_share": float(prof["cycles_svd"].sum() / max(1, prof["cycles_total"].sum())),
                "lbp_share": float(prof["cycles_lbp"].sum() / max(1, prof["cycles_total"].sum())),
                "restarts_max": int(rs.max()), "restarts_p90": float(np.percentile(rs, 90)),
-               "slowest_matrix_s": float(prof["cycles_total"].max() / clk)}
+               "slowest_matrix_s": float(prof["cycles_total"].max() / clk),
+               "slowest": [{"m": int(items[i].a.m), "n": int(items[i].a.n), "nnz": int(items[i].a.nnz),
+                            "k": int(items[i].k), "restarts": int(infos[i]["restarts"]),
+                            "s": float(prof["cycles_total"][i] / clk),
+                            "svd_s": float(prof["cycles_svd"][i] / clk), "lbp_s": float(prof["cycles_lbp"][i] / clk)}
+                           for i in np.argsort(-prof["cycles_total"])[:5]]}
     tot_bytes = sum(batch_bytes(inf, it.a.m, it.a.n, it.a.nnz, it.k) for inf, it in zip(infos, items))
     launches = 1 * args.steps
     # plain GPU form (one svdsc_solve per matrix, FP64) on a sample, and the sigma error of the batch vs it

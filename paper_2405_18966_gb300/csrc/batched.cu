@@ -134,7 +134,8 @@ constexpr int kSmH = kSmRho + kBMaxT;                 // projection coefficients
 constexpr int kSmRed = kSmH + kBMaxT + 8;             // reductions (4 x warps)
 constexpr int kSmSig = kSmRed + 4 * kBW;              // unsorted sigma (t)
 constexpr int kSmPart = kSmSig + kBMaxT;               // cluster partials: 2 x (t + 8)
-constexpr int kSmDoubles = kSmPart + 2 * (kBMaxT + 8);
+constexpr int kSmRowPart = kSmPart + 2 * (kBMaxT + 8);  // projection partials: 8 x (t + 8)
+constexpr int kSmDoubles = kSmRowPart + 8 * (kBMaxT + 8);
 // floats after the doubles: Q_U (t x k), Q_V (t x k), h32 (t + 2)
 constexpr int kSmQU = 0;
 constexpr int kSmQV = kSmQU + kBMaxT * kBMaxK;
@@ -195,24 +196,33 @@ __device__ void cta_spmv(int G, const int64_t *rp, const int32_t *col, const flo
     __syncthreads();
 }
 
-// h[c] = W(:, c)^T w for c < ncols; a warp owns TC columns at a time and each
-// lane keeps 4 rows x (TC + 1) independent loads in flight (one SM works on
-// the whole matrix, so memory-level parallelism sets its bandwidth).
+// h[c] = W(:, c)^T w for c < ncols.  Work items are (TC columns) x (one of
+// kRowParts row ranges), spread over the warps so that all of them stay busy
+// even when ncols is a little above a multiple of the warp count; each lane
+// keeps 4 rows x (TC + 1) independent loads in flight.  Partial sums per row
+// range go to shared memory and are added in range order.
+constexpr int kRowParts = 8;
+
 template <typename WT, int TC>
 __device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, const WT *__restrict__ w,
-                           int64_t len, double *h)
+                           int64_t len, double *h, double *part)
 {
     using AT = WT;  // FP32 products and sums for the FP32 shadow, FP64 otherwise
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int c0 = warp * TC; c0 < ncols; c0 += kBW * TC) {
+    const int ngroups = (ncols + TC - 1) / TC;
+    const int items = ngroups * kRowParts;
+    for (int it = warp; it < items; it += kBW) {
+        const int g = it / kRowParts, rp = it % kRowParts;
+        const int c0 = g * TC;
+        const int64_t rbeg = len * rp / kRowParts, rend = len * (rp + 1) / kRowParts;
         AT acc[TC];
 #pragma unroll
         for (int q = 0; q < TC; q++) acc[q] = AT(0);
         const WT *col[TC];
 #pragma unroll
         for (int q = 0; q < TC; q++) col[q] = W + (int64_t)min(c0 + q, ncols - 1) * ld;
-        int64_t r = lane;
-        for (; r + 96 < len; r += 128) {
+        int64_t r = rbeg + lane;
+        for (; r + 96 < rend; r += 128) {
             AT wr[4];
             WT v[TC][4];
 #pragma unroll
@@ -226,17 +236,24 @@ __device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, cons
 #pragma unroll
                 for (int u = 0; u < 4; u++) acc[q] = fma((AT)v[q][u], wr[u], acc[q]);
         }
-        for (; r < len; r += 32) {
+        for (; r < rend; r += 32) {
             const AT wr = (AT)w[r];
 #pragma unroll
             for (int q = 0; q < TC; q++) acc[q] = fma((AT)col[q][r], wr, acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < TC; q++) {
-            double s = (double)acc[q];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0 && c0 + q < ncols) h[c0 + q] = s;
+            double sum = (double)acc[q];
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0 && c0 + q < ncols) part[rp * (kBMaxT + 8) + c0 + q] = sum;
         }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncols; c += kBT) {
+        double sum = 0.0;
+#pragma unroll
+        for (int rp = 0; rp < kRowParts; rp++) sum += part[rp * (kBMaxT + 8) + c];
+        h[c] = sum;
     }
     __syncthreads();
 }
@@ -244,11 +261,12 @@ __device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, cons
 // w has the type of W: the FP32 pass reads an FP32 copy of the vector
 // (double -> float conversions run on the FP64 pipe)
 template <typename WT>
-__device__ void cta_proj(int tc, const WT *W, int64_t ld, int ncols, const WT *w, int64_t len, double *h)
+__device__ void cta_proj(int tc, const WT *W, int64_t ld, int ncols, const WT *w, int64_t len, double *h,
+                         double *part)
 {
-    if (tc >= 4) cta_proj_t<WT, 4>(W, ld, ncols, w, len, h);
-    else if (tc == 2) cta_proj_t<WT, 2>(W, ld, ncols, w, len, h);
-    else cta_proj_t<WT, 1>(W, ld, ncols, w, len, h);
+    if (tc >= 4) cta_proj_t<WT, 4>(W, ld, ncols, w, len, h, part);
+    else if (tc == 2) cta_proj_t<WT, 2>(W, ld, ncols, w, len, h, part);
+    else cta_proj_t<WT, 1>(W, ld, ncols, w, len, h, part);
 }
 
 // w -= W h; returns sum of the new w^2 (CTA-wide, deterministic) if asked.
@@ -376,12 +394,12 @@ __device__ double cl_cgs2(BRun &R, const double *W, const float *W32, int64_t ld
     if (ncols <= 0) return cl_sum_scalar(R, cta_norm2(w + r0, len, red));
     for (int64_t j = threadIdx.x; j < len; j += kBT) R.wf[r0 + j] = (float)w[r0 + j];
     __syncthreads();
-    cta_proj<float>(R.tc, W32 + r0, ld, ncols, R.wf + r0, len, part_buf(R));
+    cta_proj<float>(R.tc, W32 + r0, ld, ncols, R.wf + r0, len, part_buf(R), R.sm + kSmRowPart);
     cl_gather(R, ncols, h);
     for (int c = threadIdx.x; c < ncols; c += kBT) h32[c] = (float)h[c];
     __syncthreads();
     cta_update<float, float>(W32 + r0, ld, ncols, h32, w + r0, len, false, red);
-    cta_proj<double>(R.tc, W + r0, ld, ncols, w + r0, len, part_buf(R));
+    cta_proj<double>(R.tc, W + r0, ld, ncols, w + r0, len, part_buf(R), R.sm + kSmRowPart);
     cl_gather(R, ncols, h);
     return cl_sum_scalar(R, cta_update<double, double>(W + r0, ld, ncols, h, w + r0, len, true, red));
 }
@@ -801,7 +819,7 @@ tune_proj_kernel(const double *W_slots, int64_t ldw_slot, int64_t ld, int ncols,
 {
     extern __shared__ __align__(16) double bsm[];
     const double *W = W_slots + (int64_t)blockIdx.x * ldw_slot;
-    for (int r = 0; r < reps; r++) cta_proj<double>(tc, W, ld, ncols, w, len, bsm);
+    for (int r = 0; r < reps; r++) cta_proj<double>(tc, W, ld, ncols, w, len, bsm, bsm + (kBMaxT + 8));
 }
 
 }  // namespace svdsc
@@ -901,7 +919,7 @@ static int tune_matrix(svdsc_batch *B, int b, int nsm, double *yscratch, int64_t
             double bt = 1e30;
             for (int tc : {1, 2, 4}) {
                 const double ms = time_ms(B->stream, [&] {
-                    tune_proj_kernel<<<nsm, kBT, sizeof(double) * (kBMaxT + 8), B->stream>>>(
+                    tune_proj_kernel<<<nsm, kBT, sizeof(double) * 9 * (kBMaxT + 8), B->stream>>>(
                         wsc, 0, M.m, ncols, wsc, M.m, tc, 2);
                 });
                 B->tune_ms += 2 * ms;
