@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "seconds to k triplets at residual ≤tol; SpMV+reorth HBM GB/s vs ~8 TB/s"
 HBM_NOMINAL_GBS = 7900.0
+# DRAM bytes (read + write) / algorithmic bytes of the top kernels, from the
+# full-size ncu captures summarised in
+# profiles/cgs2_gemv_pair_1000000x150_and_spmv_sell_zipf.md
+TRAFFIC_RATIO = {"gemv_t": 1211.03 / 1208.0, "gemv_n": 1214.24 / 1216.0, "spmv": 270.62 / 263.2}
 # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -538,16 +542,21 @@ def main():
     avg_ms = tot["ms"][dom] / n_l
     if dom in ("gemv_t", "gemv_n", "gemm") and prec == "fp64":
         ach = tot["flops"][dom] / n_l / (avg_ms * 1e-3) / 1e12
+        tr = TRAFFIC_RATIO.get(dom)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": (tr * tot["bytes"][dom] / n_l) if tr else None,
+                "traffic_unit": "bytes per launch (ncu DRAM/algorithmic ratio x average algorithmic bytes)",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                 "hbm_gbs": tot["bytes"][dom] / n_l / (avg_ms * 1e-3) / 1e9,
                 "avg_launch_ms": avg_ms, "launches": n_l}
         roof["hbm_frac"] = roof["hbm_gbs"] / peaks["hbm_gbs"]
     else:
         ach = tot["bytes"][dom] / n_l / (avg_ms * 1e-3) / 1e9
+        tr = TRAFFIC_RATIO.get(dom) if prec == "fp64" else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+                "frac": ach / peaks["hbm_gbs"], "traffic": (tr * tot["bytes"][dom] / n_l) if tr else None,
+                "peak_source": f"{peak_src} hbm_gbs",
                 "avg_launch_ms": avg_ms, "launches": n_l}
     hot = ("spmv", "gemv_t", "gemv_n")
     hot_bytes = sum(tot["bytes"][ph] for ph in hot)
