@@ -145,7 +145,8 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
 /*
  * Alg. 2: k largest singular triplets.
  *   t = k + p (p < 0: t = max(15, 3k), Alg. 2 line 1); needs 1 <= k <= t,
- *   t <= m and t + 1 <= n (SVDSC_ERR_SIZE otherwise).
+ *   t <= m and t + 1 <= n, k <= 256 and t <= 512 (t <= 448 with the
+ *   tensor-core restart GEMM) (SVDSC_ERR_SIZE otherwise).
  *   tol: relative residual tolerance of Eq. (4), > 0 (the paper uses 1e-10).
  *   maxit >= 1: number of projected-SVD-and-test rounds; the last round never
  *   restarts (at most maxit - 1 restarts).

@@ -187,6 +187,7 @@ jacobi_small_kernel(int t, const double *__restrict__ T, int64_t ldt, double *__
 
 // ------------------------------------------------------------ multi-CTA form
 constexpr int kCoopThreads = 256;
+constexpr int kCoopPer = 2;  // column elements per thread: t <= 512
 
 // Bounded grid barrier for a cooperative launch (all CTAs co-resident).
 // bar[0]: arrivals, bar[1]: generation.  Gives up after ~0.5-1 s of spinning,
@@ -209,7 +210,7 @@ __device__ bool grid_sync(unsigned *bar, unsigned nblk, int *timeout)
             unsigned long long spins = 0;
             while (*vgen == gen) {
                 if (++spins > (1ull << 23)) { ok = 0; atomicExch(timeout, 1); break; }
-                __nanosleep(64);
+                if (spins > 2048) __nanosleep(32);  // poll tightly first, then back off
             }
         }
         __threadfence();
@@ -261,12 +262,24 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
                 rr_pair(slot, round, n2, &p, &q);
                 if (q >= t) continue;
                 double *bp = B + (int64_t)p * t, *bq = B + (int64_t)q * t;
+                double *wp = W + (int64_t)p * t, *wq = W + (int64_t)q * t;
+                // every element of both pairs of columns is loaded once, up front
+                // (t <= kCoopThreads * kCoopPer), and kept in registers
+                double xb[kCoopPer], yb[kCoopPer], xw[kCoopPer], yw[kCoopPer];
                 double a = 0.0, b = 0.0, g = 0.0;
-                for (int r = threadIdx.x; r < t; r += kCoopThreads) {
-                    const double x = __ldcg(bp + r), y = __ldcg(bq + r);
-                    a += x * x;
-                    b += y * y;
-                    g += x * y;
+#pragma unroll
+                for (int u = 0; u < kCoopPer; u++) {
+                    const int r = threadIdx.x + u * kCoopThreads;
+                    xb[u] = r < t ? __ldcg(bp + r) : 0.0;
+                    yb[u] = r < t ? __ldcg(bq + r) : 0.0;
+                    xw[u] = r < t ? __ldcg(wp + r) : 0.0;
+                    yw[u] = r < t ? __ldcg(wq + r) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kCoopPer; u++) {
+                    a += xb[u] * xb[u];
+                    b += yb[u] * yb[u];
+                    g += xb[u] * yb[u];
                 }
                 for (int o = 16; o > 0; o >>= 1) {
                     a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -290,16 +303,15 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
                 __syncthreads();
                 if (!do_rot) continue;
                 if (threadIdx.x == 0) atomicAdd(rot + sweeps, 1);
-                for (int r = threadIdx.x; r < t; r += kCoopThreads) {
-                    const double x = __ldcg(bp + r), y = __ldcg(bq + r);
-                    __stcg(bp + r, c * x - s * y);
-                    __stcg(bq + r, s * x + c * y);
-                }
-                double *wp = W + (int64_t)p * t, *wq = W + (int64_t)q * t;
-                for (int r = threadIdx.x; r < t; r += kCoopThreads) {
-                    const double x = __ldcg(wp + r), y = __ldcg(wq + r);
-                    __stcg(wp + r, c * x - s * y);
-                    __stcg(wq + r, s * x + c * y);
+#pragma unroll
+                for (int u = 0; u < kCoopPer; u++) {
+                    const int r = threadIdx.x + u * kCoopThreads;
+                    if (r < t) {
+                        __stcg(bp + r, c * xb[u] - s * yb[u]);
+                        __stcg(bq + r, s * xb[u] + c * yb[u]);
+                        __stcg(wp + r, c * xw[u] - s * yw[u]);
+                        __stcg(wq + r, s * xw[u] + c * yw[u]);
+                    }
                 }
             }
             if (!grid_sync(bar, nblk, timeout)) return;
@@ -368,6 +380,7 @@ cudaError_t small_svd(int t, const double *T, int64_t ldt, double *S, double *Uh
         if (launches) (*launches)++;
         return cudaGetLastError();
     }
+    if (t > kCoopThreads * kCoopPer) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(w.rot, 0, sizeof(int) * w.max_sweeps, s);

@@ -704,6 +704,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     const int t = (p < 0) ? std::max(15, 3 * k) : k + p;
     if (t < k || t > c->m || t + 1 > c->n || k > kGemmGroups * kGemmMaxQ) return SVDSC_ERR_SIZE;
     if (c->restart_gemm == 0 && t > 448) return SVDSC_ERR_SIZE;
+    if (t > 512) return SVDSC_ERR_SIZE;  // projected SVD limit
     int rc = reserve_ws(c, t);
     if (rc) return rc;
     cudaStream_t s = c->stream;
@@ -939,7 +940,7 @@ int svdsc_gemm(svdsc_ctx *c, int mode, int64_t rows, int t, int k, const double 
 int svdsc_small_svd(svdsc_ctx *c, int t, const double *T, int64_t ldt, double *S, double *Uh, double *Vh)
 {
     if (!c || t < 1 || !T || !S || !Uh || !Vh || ldt < t) return SVDSC_ERR_ARG;
-    if (t > c->t_cap) return SVDSC_ERR_SIZE;
+    if (t > c->t_cap || t > 512) return SVDSC_ERR_SIZE;
     DevStatus init;
     memset(&init, 0, sizeof(init));
     init.bd_step = INT_MAX;

@@ -24,10 +24,10 @@ __device__ __forceinline__ AT spmv_row_group(const int64_t *__restrict__ row_ptr
     AT a0 = AT(0), a1 = AT(0);
     int64_t e = e0 + lg;
     for (; e + 3 * G < e1; e += 4 * G) {  // four independent loads in flight per lane
-        const int32_t c0 = __ldg(col + e), c1 = __ldg(col + e + G), c2 = __ldg(col + e + 2 * G),
-                      c3 = __ldg(col + e + 3 * G);
-        const VT v0 = __ldg(val + e), v1 = __ldg(val + e + G), v2 = __ldg(val + e + 2 * G),
-                 v3 = __ldg(val + e + 3 * G);
+        const int32_t c0 = __ldcs(col + e), c1 = __ldcs(col + e + G), c2 = __ldcs(col + e + 2 * G),
+                      c3 = __ldcs(col + e + 3 * G);
+        const VT v0 = __ldcs(val + e), v1 = __ldcs(val + e + G), v2 = __ldcs(val + e + 2 * G),
+                 v3 = __ldcs(val + e + 3 * G);
         a0 += AT(v0) * AT(__ldg(x + c0));
         a1 += AT(v1) * AT(__ldg(x + c1));
         a0 += AT(v2) * AT(__ldg(x + c2));
@@ -83,16 +83,18 @@ csr_spmv_binned(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__
         AT a0 = AT(0), a1 = AT(0), a2 = AT(0), a3 = AT(0);
         int j = 0;
         for (; j + 3 < w; j += 4) {
-            const int32_t c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1)), c2 = __ldg(cp + 32 * (j + 2)),
-                          c3 = __ldg(cp + 32 * (j + 3));
-            const VT v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1)), v2 = __ldg(vp + 32 * (j + 2)),
-                     v3 = __ldg(vp + 32 * (j + 3));
+            // the matrix is streamed with evict-first loads so that the gathered
+            // vector x stays resident in L2
+            const int32_t c0 = __ldcs(cp + 32 * j), c1 = __ldcs(cp + 32 * (j + 1)), c2 = __ldcs(cp + 32 * (j + 2)),
+                          c3 = __ldcs(cp + 32 * (j + 3));
+            const VT v0 = __ldcs(vp + 32 * j), v1 = __ldcs(vp + 32 * (j + 1)), v2 = __ldcs(vp + 32 * (j + 2)),
+                     v3 = __ldcs(vp + 32 * (j + 3));
             a0 += AT(v0) * AT(__ldg(x + c0));
             a1 += AT(v1) * AT(__ldg(x + c1));
             a2 += AT(v2) * AT(__ldg(x + c2));
             a3 += AT(v3) * AT(__ldg(x + c3));
         }
-        for (; j < w; j++) a0 += AT(__ldg(vp + 32 * j)) * AT(__ldg(x + __ldg(cp + 32 * j)));
+        for (; j < w; j++) a0 += AT(__ldcs(vp + 32 * j)) * AT(__ldg(x + __ldcs(cp + 32 * j)));
         const int64_t r = sell_perm[i];
         const double coef = coef_dev ? *coef_dev : coef_h;
         y[r] = double((a0 + a1) + (a2 + a3)) - (z ? coef * z[r] : 0.0);
