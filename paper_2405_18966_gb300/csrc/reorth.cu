@@ -32,7 +32,12 @@ __device__ __forceinline__ bool poisoned(const int *poison)
 
 constexpr int kProjWarps = 16;
 
-// P[c * nb + b] = sum over the rows of chunk b of W(r, c) * w(r)
+// P[c * nb + b] = sum over the rows of chunk b of W(r, c) * w(r).
+// FP64: each lane keeps one accumulator per column (the FP64 pipe, at 2 FMA
+// per clock per SM on GB300, is the bound, not the FMA latency), the 32 lane
+// partials of a column go to shared memory, and one thread per column adds
+// them: 1 FP64 add per lane and column instead of a 5-step shuffle tree plus
+// merging of several accumulators.
 template <typename WT>
 __global__ void __launch_bounds__(kProjWarps * 32)
 proj_partial_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__restrict__ w,
@@ -51,26 +56,36 @@ proj_partial_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const doubl
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int c = warp; c < ncols; c += kProjWarps) {
-        const WT *col = W + (int64_t)c * ld + r0;
-        double s;
-        if constexpr (sizeof(WT) == 8) {
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if constexpr (sizeof(WT) == 8) {
+        double *lp = ws + ((R + 1) & ~int64_t(1));  // lane partials: [column][32]
+        for (int c = warp; c < ncols; c += kProjWarps) {
+            const double *col = W + (int64_t)c * ld + r0;
+            double a = 0.0;
             int j = 2 * lane;
             for (; j + 65 < rows; j += 128) {
                 const double2 v0 = __ldcs((const double2 *)(col + j));
                 const double2 v1 = __ldcs((const double2 *)(col + j + 64));
-                a0 = fma(v0.x, ws[j], a0);
-                a1 = fma(v0.y, ws[j + 1], a1);
-                a2 = fma(v1.x, ws[j + 64], a2);
-                a3 = fma(v1.y, ws[j + 65], a3);
+                a = fma(v0.x, ws[j], a);
+                a = fma(v0.y, ws[j + 1], a);
+                a = fma(v1.x, ws[j + 64], a);
+                a = fma(v1.y, ws[j + 65], a);
             }
             for (; j < rows; j += 64) {
-                a0 = fma((double)col[j], ws[j], a0);
-                if (j + 1 < rows) a1 = fma((double)col[j + 1], ws[j + 1], a1);
+                a = fma((double)col[j], ws[j], a);
+                if (j + 1 < rows) a = fma((double)col[j + 1], ws[j + 1], a);
             }
-            s = (a0 + a1) + (a2 + a3);
-        } else {
+            lp[c * 32 + lane] = a;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+            double s = 0.0;
+#pragma unroll 8
+            for (int l = 0; l < 32; l++) s += lp[c * 32 + l];
+            P[(int64_t)c * nb + blockIdx.x] = s;
+        }
+    } else {
+        for (int c = warp; c < ncols; c += kProjWarps) {
+            const WT *col = W + (int64_t)c * ld + r0;
             // FP32 shadow (first CGS pass of the mixed form): FP32 products and
             // sums, four 16-byte loads in flight per lane
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -101,11 +116,11 @@ proj_partial_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const doubl
 #pragma unroll
             for (int q = 0; q < 4; q++)
                 if (j + q < rows) a0 = fmaf((float)col[j + q], ws32[j + q], a0);
-            s = (double)((a0 + a1) + (a2 + a3));
-        }
+            double s = (double)((a0 + a1) + (a2 + a3));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) P[(int64_t)c * nb + blockIdx.x] = s;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) P[(int64_t)c * nb + blockIdx.x] = s;
+        }
     }
 }
 
@@ -113,8 +128,14 @@ void proj_partial(const double *W, int64_t ld, int ncols, const double *w, const
                   double *P, const int *poison, cudaStream_t s)
 {
     if (ncols <= 0) return;
-    proj_partial_kernel<double><<<c.nb, kProjWarps * 32, sizeof(double) * c.R, s>>>(
-        W, ld, ncols, w, c.len, c.R, c.nb, P, poison);
+    const size_t smem = sizeof(double) * (((c.R + 1) & ~int64_t(1)) + 32 * (size_t)ncols);
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        // up to 4,096 rows of w plus 32 partials for up to 513 columns: < 170 KB
+        cudaFuncSetAttribute(proj_partial_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = 200 * 1024;
+    }
+    proj_partial_kernel<double><<<c.nb, kProjWarps * 32, smem, s>>>(W, ld, ncols, w, c.len, c.R, c.nb, P, poison);
 }
 
 void proj_partial_f32(const float *W32, int64_t ld, int ncols, const double *w, const Chunk &c,
