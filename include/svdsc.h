@@ -46,6 +46,7 @@ extern "C" {
 enum svdsc_format { SVDSC_CSR = 0, SVDSC_DENSE = 1 };
 enum svdsc_precision { SVDSC_FP64 = 0, SVDSC_MIXED = 1 };
 enum svdsc_value_type { SVDSC_F64 = 0, SVDSC_F32 = 1 };
+enum svdsc_which { SVDSC_LARGEST = 0, SVDSC_SMALLEST = 1 };
 
 /*
  * Input matrix (read-only, owned by the caller; svdsc_create copies it, so
@@ -84,6 +85,12 @@ typedef struct svdsc_matrix {
  * pass, all norms, the projected SVD and the residual test stay FP64).
  * seed selects the counter-based normal generator used for v_1 when no start
  * vector is given and for replacement vectors after a breakdown.
+ * which: SVDSC_LARGEST (0) computes the k largest triplets (Alg. 2);
+ * SVDSC_SMALLEST (1) the k smallest: the projected matrix's Ritz values
+ * approximate both ends of the spectrum (Sec. 2), and the restart then keeps
+ * the k smallest Ritz triplets instead of the k largest.  SVDSC_SMALLEST needs
+ * m >= n (pass A^T for a wide matrix); svdsc_create returns SVDSC_ERR_ARG
+ * otherwise.  The batched form supports SVDSC_LARGEST only.
  */
 typedef struct svdsc_options {
     int32_t precision;
@@ -91,6 +98,7 @@ typedef struct svdsc_options {
     uint64_t seed;
     int32_t restart_gemm;  /* 0: tensor cores (svdsc_gemm modes 0/1, default); 1: FP64 FMA on CUDA cores */
     int32_t batch_cluster; /* batched form: CTAs (one cluster) per matrix, 1, 2, 4 or 8; 0 = automatic */
+    int32_t which;         /* SVDSC_LARGEST (default) or SVDSC_SMALLEST */
 } svdsc_options;
 
 /* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
@@ -143,7 +151,8 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
                  void *stream);
 
 /*
- * Alg. 2: k largest singular triplets.
+ * Alg. 2: k largest singular triplets (k smallest if the context was created
+ * with which = SVDSC_SMALLEST).
  *   t = k + p (p < 0: t = max(15, 3k), Alg. 2 line 1); needs 1 <= k <= t,
  *   t <= m and t + 1 <= n, k <= 256 and t <= 512 (t <= 448 with the
  *   tensor-core restart GEMM) (SVDSC_ERR_SIZE otherwise).
@@ -152,7 +161,8 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
  *   restarts (at most maxit - 1 restarts).
  *   v0: start vector (n entries, host or device per v0_on_device) or NULL for
  *   the seeded random draw.
- *   Outputs (written on success or SVDSC_NOT_CONVERGED): S[k] descending,
+ *   Outputs (written on success or SVDSC_NOT_CONVERGED): S[k] descending
+ *   (ascending for SVDSC_SMALLEST: the smallest first),
  *   U (m x k, column-major, ldu >= m), V (n x k, ldv >= n), res[k] (may be
  *   NULL) with res_j = |beta_t Uh(t,j)| / sigma_j.  Each pair (u_j, v_j) is
  *   signed so that the entry of v_j with the largest magnitude (lowest index

@@ -83,7 +83,7 @@ def lib():
             L.orc_jacobi_svd.argtypes = [i64, i64, vp, i64, vp, vp, i64, vp, i64, C.c_int]
             L.orc_jacobi_svd.restype = C.c_int
             L.orc_sign_normalize.argtypes = [i64, i64, i64, vp, i64, vp, i64]
-            L.orc_svds.argtypes = [C.POINTER(_Mat), i64, i64, dbl, i64, C.c_uint64, vp, i64,
+            L.orc_svds.argtypes = [C.POINTER(_Mat), i64, i64, dbl, i64, i64, C.c_uint64, vp, i64,
                                    vp, vp, i64, vp, i64, vp, C.POINTER(Info), vp, vp, vp]
             L.orc_svds.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
@@ -225,8 +225,9 @@ def subspace_dim(k: int, p: int) -> int:
 
 
 def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, seed: int = 0,
-         v0=None, step_budget: int = -1, return_basis: bool = False):
-    """Alg. 2 of the paper: k largest singular triplets of A.
+         v0=None, step_budget: int = -1, return_basis: bool = False, which: str = "largest"):
+    """Alg. 2 of the paper: k largest singular triplets of A (which="largest"),
+    or the k smallest (which="smallest", m >= n; S ascending).
 
     Returns a dict with S (k), U (m x k), V (n x k), res (k), info (dict) and,
     if ``return_basis``, the final Lanczos basis Ub (m x t), Vb (n x (t+1))
@@ -246,11 +247,13 @@ def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, seed: int
         Ub = np.zeros((m, t), order="F")
         Vb = np.zeros((n, t + 1), order="F")
         Tb = np.zeros((t + 1, t + 1), order="F")
-    rc = lib().orc_svds(C.byref(b.mat), k, p, tol, maxit, C.c_uint64(seed), _ptr(v0a),
+    wh = {"largest": 0, "smallest": 1}[which]
+    rc = lib().orc_svds(C.byref(b.mat), k, p, tol, maxit, wh, C.c_uint64(seed), _ptr(v0a),
                         step_budget, _ptr(S), _ptr(U), m, _ptr(V), n, _ptr(res),
                         C.byref(info), _ptr(Ub), _ptr(Vb), _ptr(Tb))
     if rc == -1:
-        raise ValueError("bad arguments (need 1 <= k <= t, t <= m, t + 1 <= n, tol > 0, maxit >= 1)")
+        raise ValueError("bad arguments (need 1 <= k <= t, t <= m, t + 1 <= n, tol > 0, maxit >= 1; "
+                         "m >= n for the smallest triplets)")
     if rc != 0:
         raise MemoryError("oracle ran out of memory")
     out = {"S": S, "U": U, "V": V, "res": res, "info": info.as_dict(), "t": t}

@@ -434,7 +434,11 @@ void orc_sign_normalize(int64_t m, int64_t n, int64_t k, double *U, int64_t ldu,
 }
 
 /*
- * Alg. 2: k largest singular triplets of A.
+ * Alg. 2: k largest singular triplets of A (which = 0), or the k smallest
+ * (which = 1: the Ritz values of the projected matrix approximate both ends
+ * of the spectrum, Sec. 2; the same restart keeps the k smallest Ritz
+ * triplets instead of the k largest; needs m >= n so that the n singular
+ * values of A are those of A^T A).
  *   t = k + p (p < 0: t = max(15, 3k) as in Alg. 2 line 1); requires
  *   1 <= k <= t, t + 1 <= min(m, n) ... t <= m and t + 1 <= n.
  *   maxit: number of small-SVD-and-residual-test rounds (>= 1).
@@ -445,7 +449,7 @@ void orc_sign_normalize(int64_t m, int64_t n, int64_t k, double *U, int64_t ldu,
  * Returns 0 on success (converged or not: see info), -1 on bad arguments,
  * -4 if memory ran out.
  */
-int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit,
+int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, int64_t which,
              uint64_t seed, const double *v0, int64_t step_budget,
              double *S, double *Uout, int64_t ldu, double *Vout, int64_t ldv,
              double *res, orc_info *info, double *Ubasis, double *Vbasis, double *Tout)
@@ -454,6 +458,7 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit,
     const int64_t m = A->m, n = A->n;
     int64_t t = (p < 0) ? (3 * k > 15 ? 3 * k : 15) : k + p;
     if (k < 1 || t < k || t > m || t + 1 > n || !(tol > 0.0) || maxit < 1) return -1;
+    if (which != 0 && (which != 1 || m < n)) return -1;
 
     orc_lanczos L;
     memset(&L, 0, sizeof(L));
@@ -507,13 +512,26 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit,
             for (int64_t r = 0; r < t; r++) Tt[r + c * t] = T_(&L, r, c);
         int sw = orc_jacobi_svd(t, t, Tt, t, Sh, Uh, t, Vh, t, 200);
         if (sw > info->svd_sweeps_max) info->svd_sweeps_max = sw;
-        if (Sh[0] > L.anorm) L.anorm = Sh[0];
+        const double smax = Sh[0];    /* descending order from the Jacobi SVD */
+        if (smax > L.anorm) L.anorm = smax;
+        if (which == 1) {
+            /* smallest: reverse the order of the Ritz triplets so the wanted
+               k (ascending) are the first k columns used below */
+            for (int64_t j = 0; j < t / 2; j++) {
+                const int64_t jj = t - 1 - j;
+                double x = Sh[j]; Sh[j] = Sh[jj]; Sh[jj] = x;
+                for (int64_t r = 0; r < t; r++) {
+                    x = Uh[r + j * t]; Uh[r + j * t] = Uh[r + jj * t]; Uh[r + jj * t] = x;
+                    x = Vh[r + j * t]; Vh[r + j * t] = Vh[r + jj * t]; Vh[r + jj * t] = x;
+                }
+            }
+        }
         /* line 5 / Eq. (4): res_j = |beta_t Uh(t,j)| / sigma_j */
         double beta_t = T_(&L, t - 1, t);
         info->beta_t = beta_t;
         int64_t nconv = 0;
         for (int64_t j = 0; j < k; j++) {
-            double den = Sh[j] > DBL_EPSILON * Sh[0] ? Sh[j] : DBL_EPSILON * Sh[0];
+            double den = Sh[j] > DBL_EPSILON * smax ? Sh[j] : DBL_EPSILON * smax;
             double rj = (den > 0.0) ? fabs(beta_t * Uh[(t - 1) + j * t]) / den : 0.0;
             res[j] = rj;
             if (rj < tol) nconv++;

@@ -42,6 +42,7 @@ struct svdsc_ctx {
     float *U32a = nullptr, *V32a = nullptr;
     void *gemm_ws = nullptr;
     int restart_gemm = 0;
+    int which = 0;  // 0: k largest triplets, 1: k smallest
     double *P = nullptr, *h = nullptr, *Pn = nullptr;
     double *Sh = nullptr, *Uh = nullptr, *Vh = nullptr, *res = nullptr, *rho = nullptr;
     SvdWork svd;
@@ -130,13 +131,13 @@ static inline int *poison_ptr(svdsc_ctx *c) { return &c->st->poison; }
 __global__ void residual_kernel(int t, int k, double tol, const double *__restrict__ T,
                                 const double *__restrict__ Sh, const double *__restrict__ Uh,
                                 double *__restrict__ res, double *__restrict__ rho, DevStatus *st,
-                                int parity)
+                                int parity, int imax)
 {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
     const double beta_t = T[(t - 1) + (int64_t)t * (t + 1)];
-    const double s0 = Sh[0];
+    const double s0 = Sh[imax];  // the largest Ritz value
     int local = 0;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         const double den = Sh[j] > DBL_EPSILON * s0 ? Sh[j] : DBL_EPSILON * s0;
@@ -154,6 +155,28 @@ __global__ void residual_kernel(int t, int k, double tol, const double *__restri
         st->beta_t = beta_t;
         if (s0 > st->anorm[parity]) st->anorm[parity] = s0;
     }
+}
+
+// Reverses the order of the t Ritz triplets (S ascending) so that the k
+// smallest are the first k columns the residual test, restart and outputs use.
+__global__ void reverse_triplets_kernel(int t, double *__restrict__ Sh, double *__restrict__ Uh,
+                                        double *__restrict__ Vh)
+{
+    const int half = t / 2;
+    const int64_t total = (int64_t)half * t;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i / t), r = (int)(i % t);
+        const int64_t a = r + (int64_t)j * t, b = r + (int64_t)(t - 1 - j) * t;
+        double x = Uh[a]; Uh[a] = Uh[b]; Uh[b] = x;
+        x = Vh[a]; Vh[a] = Vh[b]; Vh[b] = x;
+    }
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < half; j += blockDim.x) {
+            const double x = Sh[j];
+            Sh[j] = Sh[t - 1 - j];
+            Sh[t - 1 - j] = x;
+        }
 }
 
 // T <- 0; T(j,j) = sigma_j, T(j,k+1) = rho_j for j <= k  (Alg. 2 line 9)
@@ -635,6 +658,9 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
     c->timing = opt ? (opt->timing != 0) : false;
     c->restart_gemm = opt ? opt->restart_gemm : 0;
     if (c->restart_gemm != 0 && c->restart_gemm != 1) { delete c; return SVDSC_ERR_ARG; }
+    c->which = opt ? opt->which : SVDSC_LARGEST;
+    if ((c->which != SVDSC_LARGEST && c->which != SVDSC_SMALLEST) ||
+        (c->which == SVDSC_SMALLEST && A->m < A->n)) { delete c; return SVDSC_ERR_ARG; }
     c->format = A->format;
     c->m = A->m;
     c->n = A->n;
@@ -770,12 +796,19 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         {
             const int e0 = ph_begin(c);
             CU(small_svd(t, c->T, t + 1, c->Sh, c->Uh, c->Vh, c->svd, c->st, s, nullptr));
-            ph_end(c, SVDSC_PH_SVD, e0, 1, 0.0, 0.0);
+            int nl = 1;
+            if (c->which == SVDSC_SMALLEST) {  // wanted (smallest) triplets first, ascending
+                reverse_triplets_kernel<<<std::max(1, std::min(64, (t / 2 * t + 255) / 256)), 256, 0, s>>>(
+                    t, c->Sh, c->Uh, c->Vh);
+                nl++;
+            }
+            ph_end(c, SVDSC_PH_SVD, e0, nl, 0.0, 0.0);
         }
         // line 5: residual test (Eq. 4)
         {
             const int e0 = ph_begin(c);
-            residual_kernel<<<1, 256, 0, s>>>(t, k, tol, c->T, c->Sh, c->Uh, c->res, c->rho, c->st, c->parity);
+            residual_kernel<<<1, 256, 0, s>>>(t, k, tol, c->T, c->Sh, c->Uh, c->res, c->rho, c->st, c->parity,
+                                              c->which == SVDSC_SMALLEST ? t - 1 : 0);
             ph_end(c, SVDSC_PH_OTHER, e0, 1, 0.0, 0.0);
         }
         CU(cudaGetLastError());

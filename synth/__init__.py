@@ -227,6 +227,46 @@ def workload_dense(scale: float = 1.0) -> Dense:
     return dense_prescribed(m, n, decay_095(n), BASE_SEED + 3, name=f"dense-{m}x{n}-0.95^i")
 
 
+def decay1(n: int) -> np.ndarray:
+    """Decay1 of Eq. 16: sigma_i = 10^(-4 (i-1)/19) for i = 1..20, then 1e-4 / (i-20)^0.1."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    head = 10.0 ** (-4.0 * (i - 1.0) / 19.0)
+    tail = 1e-4 / np.maximum(i - 20.0, 1.0) ** 0.1
+    return np.where(i <= 20, head, tail)
+
+
+def decay2(n: int) -> np.ndarray:
+    """Decay2 of Eq. 16: sigma_i = i^-2."""
+    return np.arange(1, n + 1, dtype=np.float64) ** -2.0
+
+
+def decay3(n: int) -> np.ndarray:
+    """Decay3 of Eq. 16: sigma_i = i^-3."""
+    return np.arange(1, n + 1, dtype=np.float64) ** -3.0
+
+
+DECAYS = {1: decay1, 2: decay2, 3: decay3}
+
+
+def workload_dense_decay(which: int, scale: float = 1.0) -> Dense:
+    """DenseN of Sec. 5 (N = 1, 2, 3): 10,000 x 10,000 dense FP64 with the DecayN
+    spectrum of Eq. 16.  The paper does not say how its singular vectors are
+    drawn; here they are products of 4 + 4 random Householder reflectors, so the
+    exact singular values (and vectors) are known."""
+    n = max(2, int(round(10_000 * scale)))
+    return dense_prescribed(n, n, DECAYS[which](n), BASE_SEED + 10 + which,
+                            name=f"dense{which}-{n}x{n}-decay{which}")
+
+
+def repeated_spectrum(n: int) -> np.ndarray:
+    """A spectrum with exactly repeated singular values (clusters of sizes 3, 2,
+    4, 2 at the top, then a geometric tail), the kind of input on which Sec. 5
+    reports other solvers returning wrong values (many multiple singular values)."""
+    head = [3.0] * 3 + [2.0] * 2 + [1.5] * 4 + [1.25] * 2
+    tail = 1.0 * 0.97 ** np.arange(max(0, n - len(head)), dtype=np.float64)
+    return np.concatenate([np.array(head[:n]), tail])[:n]
+
+
 def workload_sparse_small_fp32() -> CSR:
     """The 2,000 x 1,000 matrix with values rounded to FP32 (exact in both precisions)."""
     a = workload_sparse_small()
