@@ -468,6 +468,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--ref-restarts", type=int, default=None)
+    ap.add_argument("--reorth", choices=["full", "partial"], default="full",
+                    help="full: CGS2 on every Lanczos vector (the paper's scheme, default); partial: the "
+                         "estimate-driven partial re-orthogonalization (opt-in)")
     ap.add_argument("--kernel", choices=["spmv", "spmv_t", "cgs2", "gemm", "gemm_mixed", "small_svd"],
                     help="time a few launches of one hot-path step through its component entry point "
                          "(for profiling) instead of whole solves")
@@ -525,12 +528,13 @@ def main():
     cfg["l2"] = "inputs larger than L2 (no flush): the matrix alone exceeds 129 MB" \
         if a_bytes > 129e6 else "small working set (L2-resident)"
     cfg["maxit"] = maxit
+    cfg["reorth"] = args.reorth
     cfg["parallelism"] = "replicas" if ws > 1 else "single-gpu"
 
     stream = torch.cuda.current_stream()
     # the headline is timed without per-launch events; a second, instrumented
     # context (timing=True) times every launch for the phase and roofline figures
-    solver = pkg.Solver(A, precision=prec, timing=False, stream=stream.cuda_stream)
+    solver = pkg.Solver(A, precision=prec, timing=False, stream=stream.cuda_stream, reorth=args.reorth)
     v0_dev = torch.tensor(v0, device="cuda")
     outs = (torch.empty(k, dtype=torch.float64, device="cuda"),
             torch.empty((k, A.m), dtype=torch.float64, device="cuda"),
@@ -560,7 +564,7 @@ def main():
     ms = allreduce_max(ms, ws)
 
     # instrumented pass: the same solves with CUDA events around every launch
-    solver_t = pkg.Solver(A, precision=prec, timing=True, stream=stream.cuda_stream)
+    solver_t = pkg.Solver(A, precision=prec, timing=True, stream=stream.cuda_stream, reorth=args.reorth)
     solver_t.solve(k, p, tol, maxit, v0=v0_dev, outputs=outs)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -627,7 +631,7 @@ def main():
         for it in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with pkg.Solver(hp, precision=prec) as s2:
+            with pkg.Solver(hp, precision=prec, reorth=args.reorth) as s2:
                 r2 = s2.solve(k, p, tol, maxit, v0=hv0, outputs=hout)
             torch.cuda.synchronize()
             if it > 0:
@@ -667,7 +671,7 @@ def main():
            "config": cfg, "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": launches, "clocks": clocks,
            "solve": {"restarts": info["restarts"], "converged": info["converged"], "nconv": info["nconv"],
-                     "instrumented_ms_per_step": ms_instr,
+                     "instrumented_ms_per_step": ms_instr, "n_reorth": info["n_reorth"],
                      "n_matvec": info["n_matvec"], "breakdowns": info["breakdowns"], "t": info["t"],
                      "phase_ms_per_step": phases_ms, "anorm_est": info["anorm_est"],
                      "sigma_1": float(r.S[0]), "sigma_k": float(r.S[k - 1])},

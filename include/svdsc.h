@@ -47,6 +47,7 @@ enum svdsc_format { SVDSC_CSR = 0, SVDSC_DENSE = 1 };
 enum svdsc_precision { SVDSC_FP64 = 0, SVDSC_MIXED = 1 };
 enum svdsc_value_type { SVDSC_F64 = 0, SVDSC_F32 = 1 };
 enum svdsc_which { SVDSC_LARGEST = 0, SVDSC_SMALLEST = 1 };
+enum svdsc_reorth { SVDSC_REORTH_FULL = 0, SVDSC_REORTH_PARTIAL = 1 };
 
 /*
  * Input matrix (read-only, owned by the caller; svdsc_create copies it, so
@@ -91,6 +92,15 @@ typedef struct svdsc_matrix {
  * the k smallest Ritz triplets instead of the k largest.  SVDSC_SMALLEST needs
  * m >= n (pass A^T for a wide matrix); svdsc_create returns SVDSC_ERR_ARG
  * otherwise.  The batched form supports SVDSC_LARGEST only.
+ * reorth: SVDSC_REORTH_FULL (0, default) re-orthogonalizes every Lanczos
+ * vector against all earlier ones with two classical Gram-Schmidt passes, the
+ * full re-orthogonalization of Sec. 2.1.  SVDSC_REORTH_PARTIAL (1) is the
+ * partial scheme of lansvd (Table 1): estimates of each new vector's inner
+ * products with the earlier ones, propagated from the Lanczos relations
+ * A V = U T and A^T U = V T^T + beta v e^T, send a vector (and the next of its
+ * kind) to the same CGS2 only when an estimate exceeds eps^(3/4); the basis
+ * is then orthogonal to ~eps^(3/4) (|u_i^T u_j| <~ 1e-11) instead of ~eps.
+ * Fewer bytes, less robust; the batched form supports SVDSC_REORTH_FULL only.
  */
 typedef struct svdsc_options {
     int32_t precision;
@@ -99,6 +109,7 @@ typedef struct svdsc_options {
     int32_t restart_gemm;  /* 0: tensor cores (svdsc_gemm modes 0/1, default); 1: FP64 FMA on CUDA cores */
     int32_t batch_cluster; /* batched form: CTAs (one cluster) per matrix, 1, 2, 4 or 8; 0 = automatic */
     int32_t which;         /* SVDSC_LARGEST (default) or SVDSC_SMALLEST */
+    int32_t reorth;        /* SVDSC_REORTH_FULL (default) or SVDSC_REORTH_PARTIAL */
 } svdsc_options;
 
 /* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
@@ -137,6 +148,7 @@ typedef struct svdsc_info {
     int64_t launches[SVDSC_NUM_PHASES];
     double bytes[SVDSC_NUM_PHASES];
     double flops[SVDSC_NUM_PHASES];
+    int64_t n_reorth;      /* Lanczos vectors re-orthogonalized against their predecessors (CGS2) */
 } svdsc_info;
 
 typedef struct svdsc_ctx svdsc_ctx;

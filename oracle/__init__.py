@@ -54,7 +54,7 @@ class Info(C.Structure):
     _fields_ = [("converged", C.c_int32), ("nconv", C.c_int32), ("restarts", C.c_int32),
                 ("breakdowns", C.c_int32), ("n_matvec", C.c_int64), ("n_steps", C.c_int64),
                 ("svd_sweeps_max", C.c_int32), ("stopped_early", C.c_int32),
-                ("anorm_est", C.c_double), ("beta_t", C.c_double)]
+                ("anorm_est", C.c_double), ("beta_t", C.c_double), ("n_reorth", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -83,7 +83,7 @@ def lib():
             L.orc_jacobi_svd.argtypes = [i64, i64, vp, i64, vp, vp, i64, vp, i64, C.c_int]
             L.orc_jacobi_svd.restype = C.c_int
             L.orc_sign_normalize.argtypes = [i64, i64, i64, vp, i64, vp, i64]
-            L.orc_svds.argtypes = [C.POINTER(_Mat), i64, i64, dbl, i64, i64, C.c_uint64, vp, i64,
+            L.orc_svds.argtypes = [C.POINTER(_Mat), i64, i64, dbl, i64, i64, i64, C.c_uint64, vp, i64,
                                    vp, vp, i64, vp, i64, vp, C.POINTER(Info), vp, vp, vp]
             L.orc_svds.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
@@ -225,9 +225,12 @@ def subspace_dim(k: int, p: int) -> int:
 
 
 def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, seed: int = 0,
-         v0=None, step_budget: int = -1, return_basis: bool = False, which: str = "largest"):
+         v0=None, step_budget: int = -1, return_basis: bool = False, which: str = "largest",
+         reorth: str = "full"):
     """Alg. 2 of the paper: k largest singular triplets of A (which="largest"),
-    or the k smallest (which="smallest", m >= n; S ascending).
+    or the k smallest (which="smallest", m >= n; S ascending).  reorth="full"
+    re-orthogonalizes every Lanczos vector (CGS2), reorth="partial" only where
+    the orthogonality estimates ask for it.
 
     Returns a dict with S (k), U (m x k), V (n x k), res (k), info (dict) and,
     if ``return_basis``, the final Lanczos basis Ub (m x t), Vb (n x (t+1))
@@ -248,7 +251,8 @@ def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, seed: int
         Vb = np.zeros((n, t + 1), order="F")
         Tb = np.zeros((t + 1, t + 1), order="F")
     wh = {"largest": 0, "smallest": 1}[which]
-    rc = lib().orc_svds(C.byref(b.mat), k, p, tol, maxit, wh, C.c_uint64(seed), _ptr(v0a),
+    ro = {"full": 0, "partial": 1}[reorth]
+    rc = lib().orc_svds(C.byref(b.mat), k, p, tol, maxit, wh, ro, C.c_uint64(seed), _ptr(v0a),
                         step_budget, _ptr(S), _ptr(U), m, _ptr(V), n, _ptr(res),
                         C.byref(info), _ptr(Ub), _ptr(Vb), _ptr(Tb))
     if rc == -1:

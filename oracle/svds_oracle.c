@@ -333,6 +333,7 @@ typedef struct {
     int32_t stopped_early;  /* 1 if the step budget ran out */
     double anorm_est;       /* largest alpha, beta or sigma seen */
     double beta_t;          /* T(t,t+1) at exit */
+    int64_t n_reorth;       /* Lanczos vectors re-orthogonalized (CGS2) */
 } orc_info;
 
 typedef struct {
@@ -345,6 +346,11 @@ typedef struct {
     double anorm;
     int64_t step_budget;    /* <0: unlimited */
     orc_info *info;
+    /* partial re-orthogonalization (reorth = 1): mu[l] estimates u_i^T u_l for
+       the newest u_i, nu[l] estimates v_j^T v_l for the newest v_j */
+    int reorth;
+    double *mu, *nu;
+    int force_u, force_v;
 } orc_lanczos;
 
 #define T_(L, i, j) ((L)->T[(i) + (j) * ((L)->t + 1)])
@@ -386,6 +392,83 @@ static double orc_finish_vector(orc_lanczos *L, double *w, int64_t len, double *
     return nrm;
 }
 
+/* ------------------------------------------- partial re-orthogonalization
+ *
+ * Opt-in alternative to re-orthogonalizing every vector (the scheme of
+ * lansvd, Table 1).  The Lanczos relations A v_l = sum_r T(r,l) u_r and
+ * A^T u_l = sum_r T(l,r) v_r (both also hold after an augmented restart, where
+ * T carries the spike column of Eq. 6-7) turn into recurrences for the inner
+ * products of the newest vector with the earlier ones:
+ *   beta_i (v_{i+1}^T v_l) = u_i^T A v_l - alpha_i v_i^T v_l
+ *                          = sum_r T(r,l) (u_i^T u_r) - alpha_i (v_i^T v_l)
+ *   alpha_{i+1} (u_{i+1}^T u_l) = v_{i+1}^T A^T u_l - beta_i u_i^T u_l
+ *                          = sum_r T(l,r) (v_{i+1}^T v_r) - beta_i (u_i^T u_l)
+ * Each estimate also grows by a rounding term eps ||A|| / (divisor), signed
+ * like the estimate.  A vector is re-orthogonalized (CGS2 against all earlier
+ * ones) when its largest estimate exceeds eps^(3/4), and so is the next
+ * vector of the same kind; the estimates of a re-orthogonalized vector are
+ * reset to eps.  beta_i / alpha_{i+1} here are the norms before any
+ * re-orthogonalization.  The level eps^(3/4) (not the sqrt(eps) that
+ * suffices for accurate singular values) keeps the components CGS2 removes,
+ * which the bidiagonal T does not record, small enough that the true
+ * residuals A v - sigma u stay at ~1e-12 ||A|| instead of ~sqrt(eps) ||A||.
+ */
+#define ORC_PR_EPS DBL_EPSILON
+#define ORC_PR_DELTA 1.8189894035458565e-12  /* DBL_EPSILON^(3/4) = 2^-39 */
+
+/* nu <- estimates of v_{i+1}^T v_l, l = 1..i (i 1-based); returns 1 when
+ * v_{i+1} must be re-orthogonalized. */
+static int orc_pr_nu(orc_lanczos *L, int64_t i, double beta)
+{
+    if (!(beta > 0.0) || !isfinite(beta)) return 1;
+    const double tau = ORC_PR_EPS * L->anorm / beta;
+    const double alpha_i = T_(L, i - 1, i - 1);
+    double mx = 0.0;
+    for (int64_t l = 1; l <= i; l++) {
+        double s = 0.0;
+        for (int64_t r = 1; r <= l; r++) s += T_(L, r - 1, l - 1) * L->mu[r - 1];
+        double x = (s - alpha_i * L->nu[l - 1]) / beta;
+        x += (x >= 0.0) ? tau : -tau;
+        L->nu[l - 1] = x;
+        if (fabs(x) > mx) mx = fabs(x);
+    }
+    L->nu[i] = 1.0;
+    return (mx > ORC_PR_DELTA) || L->force_v;
+}
+
+/* mu <- estimates of u_{i+1}^T u_l, l = 1..i, from nu (v_{i+1}^T v_r,
+ * r = 1..i+1); returns 1 when u_{i+1} must be re-orthogonalized. */
+static int orc_pr_mu(orc_lanczos *L, int64_t i, double alpha)
+{
+    if (!(alpha > 0.0) || !isfinite(alpha)) return 1;
+    const double tau = ORC_PR_EPS * L->anorm / alpha;
+    const double beta_i = T_(L, i - 1, i);
+    double mx = 0.0;
+    for (int64_t l = 1; l <= i; l++) {
+        double s = 0.0;
+        for (int64_t r = l; r <= i + 1; r++) s += T_(L, l - 1, r - 1) * L->nu[r - 1];
+        double x = (s - beta_i * L->mu[l - 1]) / alpha;
+        x += (x >= 0.0) ? tau : -tau;
+        L->mu[l - 1] = x;
+        if (fabs(x) > mx) mx = fabs(x);
+    }
+    L->mu[i] = 1.0;
+    return (mx > ORC_PR_DELTA) || L->force_u;
+}
+
+/* Re-orthogonalizes w against the first `ncols` columns of W when `need`,
+ * keeping the estimates and the force flag of its kind. */
+static void orc_pr_apply(orc_lanczos *L, int need, int64_t len, int64_t ncols, const double *W,
+                         double *w, double *est, int *force)
+{
+    if (need) {
+        orc_cgs2(len, ncols, W, len, w, L->h);
+        L->info->n_reorth++;
+        for (int64_t l = 0; l < ncols; l++) est[l] = ORC_PR_EPS;
+        *force = !*force;   /* a triggered re-orthogonalization also forces the next one */
+    }
+}
+
 /* Alg. 1 loop body for i = s..t (1-based): given u_1..u_s, v_1..v_s and
  * alpha_s = T(s,s), form v_{s+1}, u_{s+1}, ..., v_{t+1}. */
 static void orc_lbp_from(orc_lanczos *L, int64_t s)
@@ -398,8 +481,17 @@ static void orc_lbp_from(orc_lanczos *L, int64_t s)
         orc_matvec_t(L->A, L->U + (i - 1) * m, L->wn);
         L->info->n_matvec++;
         for (int64_t r = 0; r < n; r++) L->wn[r] -= alpha_i * L->V[r + (i - 1) * n];
-        orc_cgs2(n, i, L->V, n, L->wn, L->h);
+        if (L->reorth) {
+            const int need = orc_pr_nu(L, i, orc_norm2(n, L->wn));
+            orc_pr_apply(L, need, n, i, L->V, L->wn, L->nu, &L->force_v);
+        } else {
+            orc_cgs2(n, i, L->V, n, L->wn, L->h);
+            L->info->n_reorth++;
+        }
+        const int32_t bdv = L->info->breakdowns;
         double beta_i = orc_finish_vector(L, L->wn, n, L->V, i);
+        if (L->reorth && L->info->breakdowns != bdv)  /* a fresh orthogonalized vector */
+            for (int64_t l = 0; l < i; l++) L->nu[l] = ORC_PR_EPS;
         T_(L, i - 1, i) = beta_i;
         L->info->n_steps++;
         if (i == t) break;  /* u_{t+1} is never used */
@@ -408,8 +500,17 @@ static void orc_lbp_from(orc_lanczos *L, int64_t s)
         orc_matvec(L->A, L->V + i * n, L->wm);
         L->info->n_matvec++;
         for (int64_t r = 0; r < m; r++) L->wm[r] -= beta_i * L->U[r + (i - 1) * m];
-        orc_cgs2(m, i, L->U, m, L->wm, L->h);
+        if (L->reorth) {
+            const int need = orc_pr_mu(L, i, orc_norm2(m, L->wm));
+            orc_pr_apply(L, need, m, i, L->U, L->wm, L->mu, &L->force_u);
+        } else {
+            orc_cgs2(m, i, L->U, m, L->wm, L->h);
+            L->info->n_reorth++;
+        }
+        const int32_t bdu = L->info->breakdowns;
         double alpha_next = orc_finish_vector(L, L->wm, m, L->U, i);
+        if (L->reorth && L->info->breakdowns != bdu)
+            for (int64_t l = 0; l < i; l++) L->mu[l] = ORC_PR_EPS;
         T_(L, i, i) = alpha_next;
         L->info->n_steps++;
     }
@@ -442,6 +543,8 @@ void orc_sign_normalize(int64_t m, int64_t n, int64_t k, double *U, int64_t ldu,
  *   t = k + p (p < 0: t = max(15, 3k) as in Alg. 2 line 1); requires
  *   1 <= k <= t, t + 1 <= min(m, n) ... t <= m and t + 1 <= n.
  *   maxit: number of small-SVD-and-residual-test rounds (>= 1).
+ *   reorth: 0 re-orthogonalizes every Lanczos vector (CGS2, Sec. 2.1); 1 only
+ *   where the partial re-orthogonalization estimates ask for it (see above).
  *   v0: start vector (length n) or NULL for the seeded random draw 0.
  *   Outputs: S (k), U (m x k, ldu), V (n x k, ldv), res (k).
  *   Optional (may be NULL): Ubasis (m x t), Vbasis (n x (t+1)),
@@ -450,7 +553,7 @@ void orc_sign_normalize(int64_t m, int64_t n, int64_t k, double *U, int64_t ldu,
  * -4 if memory ran out.
  */
 int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, int64_t which,
-             uint64_t seed, const double *v0, int64_t step_budget,
+             int64_t reorth, uint64_t seed, const double *v0, int64_t step_budget,
              double *S, double *Uout, int64_t ldu, double *Vout, int64_t ldv,
              double *res, orc_info *info, double *Ubasis, double *Vbasis, double *Tout)
 {
@@ -459,17 +562,21 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
     int64_t t = (p < 0) ? (3 * k > 15 ? 3 * k : 15) : k + p;
     if (k < 1 || t < k || t > m || t + 1 > n || !(tol > 0.0) || maxit < 1) return -1;
     if (which != 0 && (which != 1 || m < n)) return -1;
+    if (reorth != 0 && reorth != 1) return -1;
 
     orc_lanczos L;
     memset(&L, 0, sizeof(L));
     L.A = A; L.m = m; L.n = n; L.t = t; L.seed = seed; L.info = info;
     L.step_budget = step_budget;
+    L.reorth = (int)reorth;
     L.U = (double *)calloc((size_t)(m * t), sizeof(double));
     L.V = (double *)calloc((size_t)(n * (t + 1)), sizeof(double));
     L.T = (double *)calloc((size_t)((t + 1) * (t + 1)), sizeof(double));
     L.h = (double *)calloc((size_t)(t + 2), sizeof(double));
     L.wm = (double *)calloc((size_t)m, sizeof(double));
     L.wn = (double *)calloc((size_t)n, sizeof(double));
+    L.mu = (double *)calloc((size_t)(t + 2), sizeof(double));
+    L.nu = (double *)calloc((size_t)(t + 2), sizeof(double));
     double *Uh = (double *)calloc((size_t)(t * t), sizeof(double));
     double *Vh = (double *)calloc((size_t)(t * t), sizeof(double));
     double *Sh = (double *)calloc((size_t)t, sizeof(double));
@@ -477,9 +584,9 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
     double *Uk = (double *)calloc((size_t)(m * k), sizeof(double));
     double *Vk = (double *)calloc((size_t)(n * k), sizeof(double));
     double *rho = (double *)calloc((size_t)k, sizeof(double));
-    if (!L.U || !L.V || !L.T || !L.h || !L.wm || !L.wn || !Uh || !Vh || !Sh || !Tt ||
-        !Uk || !Vk || !rho) {
-        free(L.U); free(L.V); free(L.T); free(L.h); free(L.wm); free(L.wn);
+    if (!L.U || !L.V || !L.T || !L.h || !L.wm || !L.wn || !L.mu || !L.nu || !Uh || !Vh || !Sh ||
+        !Tt || !Uk || !Vk || !rho) {
+        free(L.U); free(L.V); free(L.T); free(L.h); free(L.wm); free(L.wn); free(L.mu); free(L.nu);
         free(Uh); free(Vh); free(Sh); free(Tt); free(Uk); free(Vk); free(rho);
         return -4;
     }
@@ -501,6 +608,8 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
     info->n_matvec++;
     T_(&L, 0, 0) = orc_finish_vector(&L, L.wm, m, L.U, 0);
     info->n_steps++;
+    L.nu[0] = 1.0;   /* v_1^T v_1 */
+    L.mu[0] = 1.0;   /* u_1^T u_1 */
     /* Alg. 2 line 2: LBP(A, t+1) */
     orc_lbp_from(&L, 1);
 
@@ -543,6 +652,17 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
         /* lines 8-12: augmented restart */
         orc_gemm_nn(m, t, k, L.U, m, Uh, t, Uk, m);          /* U~_k = U(:,1:t) Uh(:,1:k) */
         orc_gemm_nn(n, t, k, L.V, n, Vh, t, Vk, n);          /* V~_k = V(:,1:t) Vh(:,1:k) */
+        if (L.reorth) {
+            /* v_{k+1} = v_{t+1} against V~_k: |v~_j^T v_{t+1}| <= sum_l |Vh(l,j)| |nu_l| */
+            for (int64_t j = 0; j < k; j++) {
+                double acc = 0.0;
+                for (int64_t l = 0; l < t; l++) acc += fabs(Vh[l + j * t]) * fabs(L.nu[l]);
+                L.h[j] = acc + ORC_PR_EPS;
+            }
+            for (int64_t j = 0; j < k; j++) L.nu[j] = L.h[j];
+            L.nu[k] = 1.0;
+            L.force_u = L.force_v = 0;
+        }
         for (int64_t j = 0; j < k; j++) rho[j] = beta_t * Uh[(t - 1) + j * t];
         memset(L.T, 0, sizeof(double) * (size_t)((t + 1) * (t + 1)));
         for (int64_t j = 0; j < k; j++) {
@@ -559,7 +679,10 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
         info->n_matvec++;
         orc_gemv_n_sub(m, k, L.U, m, rho, L.wm);
         orc_cgs2(m, k, L.U, m, L.wm, L.h);
+        info->n_reorth++;
         T_(&L, k, k) = orc_finish_vector(&L, L.wm, m, L.U, k);
+        for (int64_t j = 0; j < k; j++) L.mu[j] = ORC_PR_EPS;
+        L.mu[k] = 1.0;
         info->n_steps++;
         info->restarts++;
         /* line 12: continue Alg. 1 from i = k+1 */
@@ -577,7 +700,7 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
     if (Vbasis) memcpy(Vbasis, L.V, sizeof(double) * (size_t)(n * (t + 1)));
     if (Tout) memcpy(Tout, L.T, sizeof(double) * (size_t)((t + 1) * (t + 1)));
 
-    free(L.U); free(L.V); free(L.T); free(L.h); free(L.wm); free(L.wn);
+    free(L.U); free(L.V); free(L.T); free(L.h); free(L.wm); free(L.wn); free(L.mu); free(L.nu);
     free(Uh); free(Vh); free(Sh); free(Tt); free(Uk); free(Vk); free(rho);
     return 0;
 }

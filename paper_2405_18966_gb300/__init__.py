@@ -46,7 +46,8 @@ class SvdscMatrix(C.Structure):
 
 class SvdscOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("timing", C.c_int32), ("seed", C.c_uint64),
-                ("restart_gemm", C.c_int32), ("batch_cluster", C.c_int32), ("which", C.c_int32)]
+                ("restart_gemm", C.c_int32), ("batch_cluster", C.c_int32), ("which", C.c_int32),
+                ("reorth", C.c_int32)]
 
 
 NUM_PHASES = 8
@@ -59,7 +60,8 @@ class SvdscInfo(C.Structure):
                 ("n_launches", C.c_int64), ("anorm_est", C.c_double), ("beta_t", C.c_double),
                 ("t", C.c_int32), ("reserved", C.c_int32),
                 ("ms", C.c_double * NUM_PHASES), ("launches", C.c_int64 * NUM_PHASES),
-                ("bytes", C.c_double * NUM_PHASES), ("flops", C.c_double * NUM_PHASES)]
+                ("bytes", C.c_double * NUM_PHASES), ("flops", C.c_double * NUM_PHASES),
+                ("n_reorth", C.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_
@@ -149,7 +151,7 @@ class Solver:
     """A matrix prepared on the device (svdsc_create) that can be solved many times."""
 
     def __init__(self, A, precision: str = "fp64", seed: int = 0, stream=None, timing: bool = False,
-                 restart_gemm: str = "tensor", which: str = "largest"):
+                 restart_gemm: str = "tensor", which: str = "largest", reorth: str = "full"):
         self._keep = []
         self.handle = C.c_void_p()
         prec = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -187,7 +189,7 @@ class Solver:
             mat.value_type = F64
             self.m, self.n = int(a.shape[0]), int(a.shape[1])
         opt = SvdscOptions(prec, int(timing), seed, {"tensor": 0, "fma": 1}[restart_gemm], 0,
-                           {"largest": 0, "smallest": 1}[which])
+                           {"largest": 0, "smallest": 1}[which], {"full": 0, "partial": 1}[reorth])
         st = None if stream is None else C.c_void_p(int(stream))
         self.stream = stream
         _check(lib().svdsc_create(C.byref(self.handle), C.byref(mat), C.byref(opt), st), "svdsc_create")
@@ -318,7 +320,7 @@ class Batch:
         self.k = np.ascontiguousarray(k, dtype=np.int32)
         self.p = np.ascontiguousarray(p if p is not None else self.k, dtype=np.int32)
         self.shapes = [(int(a.m), int(a.n)) for a in mats]
-        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0)
+        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0, 0)
         self.handle = C.c_void_p()
         _check(lib().svdsc_batch_create(C.byref(self.handle), nb, arr, _ptr(self.k), _ptr(self.p),
                                         C.byref(opt), None), "svdsc_batch_create")
@@ -385,7 +387,8 @@ class Batch:
 
 def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, precision: str = "fp64",
          seed: int = 0, v0=None, out: str = "host", restart_gemm: str = "tensor",
-         which: str = "largest") -> Result:
+         which: str = "largest", reorth: str = "full") -> Result:
     """One-shot convenience: create, solve, destroy."""
-    with Solver(A, precision=precision, seed=seed, restart_gemm=restart_gemm, which=which) as s:
+    with Solver(A, precision=precision, seed=seed, restart_gemm=restart_gemm, which=which,
+                reorth=reorth) as s:
         return s.solve(k, p, tol, maxit, v0=v0, out=out)

@@ -967,6 +967,7 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     *out = nullptr;
     if (opt && opt->precision != SVDSC_MIXED) return SVDSC_ERR_ARG;  // the batched form is the mixed one
     if (opt && opt->which != SVDSC_LARGEST) return SVDSC_ERR_ARG;    // and keeps the largest triplets
+    if (opt && opt->reorth != SVDSC_REORTH_FULL) return SVDSC_ERR_ARG;  // with full re-orthogonalization
     for (int b = 0; b < nb; b++) {
         const svdsc_matrix &a = As[b];
         if (a.format != SVDSC_CSR || a.m < 1 || a.n < 1) return SVDSC_ERR_ARG;

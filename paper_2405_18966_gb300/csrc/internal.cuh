@@ -43,6 +43,15 @@ struct DevStatus {
     double last_norm;  // norm of the last finalized vector
 };
 
+// Partial re-orthogonalization state (device memory).
+struct PrState {
+    double bytes_t, bytes_n, flops;  // algorithmic bytes / flops of the CGS2 passes that ran
+    int gate;      // 1: the CGS2 kernels of the current vector skip their work
+    int force_u;   // the next u vector is re-orthogonalized regardless of its estimates
+    int force_v;   // likewise for the next v vector
+    int n_reorth;  // vectors the estimates sent to CGS2 in this solve
+};
+
 // Row chunking of one vector length for the row-blocked kernels.
 struct Chunk {
     int64_t len = 0;
@@ -123,6 +132,13 @@ void norm_partial(const double *w, const Chunk &c, double *Pn, const int *poison
 void finalize(double *w, const Chunk &c, const double *Pn, double *T_entry, DevStatus *st,
               int step, int parity, int mode, float *w32, cudaStream_t s);
 void rng_normal_vec(uint64_t seed, uint64_t draw, int64_t len, double *x, cudaStream_t s);
+// partial re-orthogonalization (side 1: v vector, 0: u vector; i, kk 1-based step / restart size)
+// (bt, bn, fl: algorithmic GEMV-T / GEMV-N bytes and flops of the CGS2 if it runs)
+void pr_omega(int side, int i, int kk, const double *T, int ldt, double *mu, double *nu, const Chunk &c,
+              const double *Pn, const DevStatus *st, int parity, PrState *pr, double bt, double bn,
+              double fl, cudaStream_t s);
+void pr_restart(int t, int k, const double *Vh, double *mu, double *nu, PrState *pr, cudaStream_t s);
+void pr_reset(int side, int col, double *mu, double *nu, PrState *pr, cudaStream_t s);
 void copy_f64_to_f32(const double *x, float *y, int64_t len, cudaStream_t s);
 
 // ---- projected SVD (small_svd.cu)

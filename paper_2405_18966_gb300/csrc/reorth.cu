@@ -349,6 +349,168 @@ void finalize(double *w, const Chunk &c, const double *Pn, double *T_entry, DevS
                                                  mode, w32);
 }
 
+// ------------------------------------------- partial re-orthogonalization
+//
+// Opt-in alternative to re-orthogonalizing every Lanczos vector (the scheme
+// lansvd uses, Table 1).  With A v_l = sum_r T(r,l) u_r and
+// A^T u_l = sum_r T(l,r) v_r (true also after an augmented restart, whose T
+// has the spike column of Eq. 6-7), the inner products of a new vector with
+// the earlier ones follow
+//   ||w|| nu'_l = sum_{r<=l} T(r,l) mu_r - alpha_i nu_l         (v_{i+1}, l <= i)
+//   ||w|| mu'_l = sum_{r>=l} T(l,r) nu_r - beta_i  mu_l         (u_{i+1}, l <= i)
+// (w: the vector before normalization), each grown by a rounding term
+// eps ||A|| / ||w|| of the estimate's sign.  When the largest estimate passes
+// eps^(3/4), the vector gets the full CGS2 against all earlier ones (and so
+// does the next vector of its kind), and its estimates drop to eps.  (At
+// sqrt(eps) the singular values stay accurate, but the components CGS2 then
+// removes, which T does not record, leave true residuals near sqrt(eps)||A||;
+// eps^(3/4) keeps them near 1e-12 ||A|| for a few more CGS2 passes.)  One CTA;
+// T is bidiagonal except for the spike column kk + 1 after a restart (kk = 0
+// before the first), so only its non-zero entries are visited, in ascending
+// order.  The decision goes to pr->gate (0: run the CGS2 kernels, 1: skip).
+
+constexpr double kPrEps = 2.220446049250313e-16;      // DBL_EPSILON
+constexpr double kPrDelta = 1.8189894035458565e-12;   // DBL_EPSILON^(3/4) = 2^-39
+
+__global__ void __launch_bounds__(kRowThreads)
+pr_omega_kernel(int side, int i, int kk, const double *__restrict__ T, int ldt, double *__restrict__ mu,
+                double *__restrict__ nu, const double *__restrict__ Pn, int nb, const DevStatus *st,
+                int parity, PrState *pr, double bt, double bn, double fl)
+{
+    __shared__ double red[kRowThreads / 32];
+    __shared__ double s_w, s_mx;
+    if (*(volatile const int *)&st->poison) {
+        if (threadIdx.x == 0) pr->gate = 1;
+        return;
+    }
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kRowThreads) v += Pn[b];
+    const double tot = block_sum_256(v, red);
+    if (threadIdx.x == 0) s_w = sqrt(tot);
+    __syncthreads();
+    const double wn = s_w;
+    auto Tv = [&](int r, int c) { return T[(r - 1) + (int64_t)(c - 1) * ldt]; };  // 1-based
+    const bool ok = wn > 0.0 && isfinite(wn);
+    double mx = 0.0;
+    if (ok) {
+        const double tau = kPrEps * st->anorm[parity] / wn;
+        if (side == 1) {
+            const double alpha_i = Tv(i, i);
+            for (int l = 1 + threadIdx.x; l <= i; l += blockDim.x) {
+                double s = 0.0;
+                if (kk > 0 && l == kk + 1) {
+                    for (int r = 1; r <= l; r++) s += Tv(r, l) * mu[r - 1];
+                } else {
+                    if (l > 1 && l - 1 > kk) s += Tv(l - 1, l) * mu[l - 2];
+                    s += Tv(l, l) * mu[l - 1];
+                }
+                double x = (s - alpha_i * nu[l - 1]) / wn;
+                x += x >= 0.0 ? tau : -tau;
+                nu[l - 1] = x;
+                mx = fmax(mx, fabs(x));
+            }
+        } else {
+            const double beta_i = Tv(i, i + 1);
+            for (int l = 1 + threadIdx.x; l <= i; l += blockDim.x) {
+                double s = Tv(l, l) * nu[l - 1];
+                if (l <= kk) s += Tv(l, kk + 1) * nu[kk];
+                else s += Tv(l, l + 1) * nu[l];
+                double x = (s - beta_i * mu[l - 1]) / wn;
+                x += x >= 0.0 ? tau : -tau;
+                mu[l - 1] = x;
+                mx = fmax(mx, fabs(x));
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) m2 = fmax(m2, red[w]);
+        s_mx = m2;
+    }
+    __syncthreads();
+    int *force = side ? &pr->force_v : &pr->force_u;
+    const bool need = !ok || s_mx > kPrDelta || *force;
+    double *est = side ? nu : mu;
+    if (need)
+        for (int l = threadIdx.x; l < i; l += blockDim.x) est[l] = kPrEps;
+    if (threadIdx.x == 0) {
+        est[i] = 1.0;
+        pr->gate = need ? 0 : 1;
+        if (need) {
+            pr->n_reorth++;
+            pr->bytes_t += bt;
+            pr->bytes_n += bn;
+            pr->flops += fl;
+            *force = !*force;
+        }
+    }
+}
+
+void pr_omega(int side, int i, int kk, const double *T, int ldt, double *mu, double *nu, const Chunk &c,
+              const double *Pn, const DevStatus *st, int parity, PrState *pr, double bt, double bn,
+              double fl, cudaStream_t s)
+{
+    pr_omega_kernel<<<1, kRowThreads, 0, s>>>(side, i, kk, T, ldt, mu, nu, Pn, c.nb, st, parity, pr, bt,
+                                              bn, fl);
+}
+
+// After an augmented restart: v_{k+1} = v_{t+1} against V~_k = V(:,1:t) Vh(:,1:k)
+// is bounded by sum_l |Vh(l,j)| |nu_l| (+ eps); u_{k+1} gets CGS2 (eps).
+__global__ void __launch_bounds__(kRowThreads)
+pr_restart_kernel(int t, int k, const double *__restrict__ Vh, double *__restrict__ mu,
+                  double *__restrict__ nu, PrState *pr)
+{
+    __shared__ double anu[512];
+    for (int l = threadIdx.x; l < t; l += blockDim.x) anu[l] = fabs(nu[l]);
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        double acc = 0.0;
+        for (int l = 0; l < t; l++) acc += fabs(Vh[l + (int64_t)j * t]) * anu[l];
+        nu[j] = acc + kPrEps;
+        mu[j] = kPrEps;
+    }
+    if (threadIdx.x == 0) {
+        nu[k] = 1.0;
+        mu[k] = 1.0;
+        pr->force_u = 0;
+        pr->force_v = 0;
+    }
+}
+
+void pr_restart(int t, int k, const double *Vh, double *mu, double *nu, PrState *pr, cudaStream_t s)
+{
+    pr_restart_kernel<<<1, kRowThreads, 0, s>>>(t, k, Vh, mu, nu, pr);
+}
+
+// est[0..col-1] = eps (a vector that was orthogonalized against all earlier ones);
+// col < 0: start of a solve (nu_1 = mu_1 = 1, flags and counter cleared).
+__global__ void pr_reset_kernel(int side, int col, double *mu, double *nu, PrState *pr)
+{
+    if (col < 0) {
+        if (threadIdx.x == 0) {
+            mu[0] = 1.0;
+            nu[0] = 1.0;
+            pr->gate = 1;
+            pr->force_u = pr->force_v = 0;
+            pr->n_reorth = 0;
+            pr->bytes_t = pr->bytes_n = pr->flops = 0.0;
+        }
+        return;
+    }
+    double *est = side ? nu : mu;
+    for (int l = threadIdx.x; l < col; l += blockDim.x) est[l] = kPrEps;
+}
+
+void pr_reset(int side, int col, double *mu, double *nu, PrState *pr, cudaStream_t s)
+{
+    pr_reset_kernel<<<1, 256, 0, s>>>(side, col, mu, nu, pr);
+}
+
 // ---------------------------------------------------------------- random draws
 
 __global__ void rng_normal_kernel(uint64_t seed, uint64_t draw, int64_t len, double *x)

@@ -43,6 +43,10 @@ struct svdsc_ctx {
     void *gemm_ws = nullptr;
     int restart_gemm = 0;
     int which = 0;  // 0: k largest triplets, 1: k smallest
+    int reorth = 0; // 0: CGS2 on every Lanczos vector, 1: partial (estimate-driven)
+    double *mu = nullptr, *nu = nullptr;  // partial re-orthogonalization estimates (t + 2 each)
+    PrState *pr = nullptr;
+    int pr_kk = 0;  // size of the last augmented restart (spike column kk + 1 of T), 0 before
     double *P = nullptr, *h = nullptr, *Pn = nullptr;
     double *Sh = nullptr, *Uh = nullptr, *Vh = nullptr, *res = nullptr, *rho = nullptr;
     SvdWork svd;
@@ -361,6 +365,9 @@ static void free_workspace(svdsc_ctx *c)
     cudaFree(c->Sh); cudaFree(c->Uh); cudaFree(c->Vh); cudaFree(c->res); cudaFree(c->rho);
     cudaFree(c->svd.B); cudaFree(c->svd.W); cudaFree(c->svd.sig); cudaFree(c->svd.rot);
     cudaFree(c->svd.bar);
+    cudaFree(c->mu); cudaFree(c->nu); cudaFree(c->pr);
+    c->mu = c->nu = nullptr;
+    c->pr = nullptr;
     c->U = c->V = c->T = c->P = c->h = c->Pn = c->Sh = c->Uh = c->Vh = c->res = c->rho = nullptr;
     c->U32 = c->V32 = nullptr;
     c->svd.B = c->svd.W = c->svd.sig = nullptr;
@@ -394,6 +401,9 @@ static int reserve_ws(svdsc_ctx *c, int t)
     }
     alloc((void **)&c->P, sizeof(double) * (size_t)nbmax * cols);
     alloc((void **)&c->h, sizeof(double) * cols);
+    alloc((void **)&c->mu, sizeof(double) * cols);
+    alloc((void **)&c->nu, sizeof(double) * cols);
+    alloc((void **)&c->pr, sizeof(PrState));
     alloc((void **)&c->Pn, sizeof(double) * nbmax);
     alloc((void **)&c->Sh, sizeof(double) * t);
     alloc((void **)&c->Uh, sizeof(double) * (size_t)t * t);
@@ -450,10 +460,11 @@ static int apply_A(svdsc_ctx *c, int trans, const double *x, const float *x32, c
 
 // One CGS pass: h = W^T w, then w -= W h (Pn: partial sums of the new ||w||^2).
 static void cgs_pass(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, int ncols, double *w,
-                     const Chunk &ch, double *Pn, const int *poison)
+                     const Chunk &ch, double *Pn, const int *poison, bool count = true)
 {
     cudaStream_t s = c->stream;
-    const double L = (double)ch.len, nc = ncols;
+    // gated passes (partial re-orthogonalization) count their bytes on the device
+    const double L = count ? (double)ch.len : 0.0, nc = ncols;
     const double wsz = W32 ? 4.0 : 8.0;
     int e0 = ph_begin(c);
     if (W32) proj_partial_f32(W32, ld, ncols, w, ch, c->P, poison, s);
@@ -471,11 +482,11 @@ static void cgs_pass(svdsc_ctx *c, const double *W, const float *W32, int64_t ld
 // CGS2: w <- (I - W W^T)^2 w against ncols columns; leaves the partial sums
 // of ||w||^2 in c->Pn.  MIXED: first pass on the FP32 shadow W32.
 static void cgs2(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, int ncols, double *w,
-                 const Chunk &ch, const int *poison)
+                 const Chunk &ch, const int *poison, bool count = true)
 {
     if (ncols > 0) {
-        cgs_pass(c, W, W32, ld, ncols, w, ch, nullptr, poison);
-        cgs_pass(c, W, nullptr, ld, ncols, w, ch, c->Pn, poison);
+        cgs_pass(c, W, W32, ld, ncols, w, ch, nullptr, poison, count);
+        cgs_pass(c, W, nullptr, ld, ncols, w, ch, c->Pn, poison, count);
     } else {
         const int e0 = ph_begin(c);
         norm_partial(w, ch, c->Pn, poison, c->stream);
@@ -497,26 +508,51 @@ static void do_finalize(svdsc_ctx *c, int side, int col, double *T_entry, int mo
     c->n_steps++;
 }
 
-// v_{i+1} = A^T u_i - alpha_i v_i, CGS2 against v_1..v_i, beta_i = ||.||  (Alg. 1 lines 5-6)
+// Re-orthogonalization of a new Lanczos vector w against the first ncols
+// columns of its basis: always (CGS2), or, in the partial mode, behind the
+// estimate-driven gate of pr_omega (side 1: v vector, 0: u vector).
+static void reorth_vector(svdsc_ctx *c, int side, int ncols, double *w)
+{
+    const Chunk &ch = side ? c->cn : c->cm;
+    const double *W = side ? c->V : c->U;
+    const float *W32 = side ? c->V32 : c->U32;
+    const int64_t ld = side ? c->ldv : c->ldu;
+    if (!c->reorth) {
+        cgs2(c, W, W32, ld, ncols, w, ch, poison_ptr(c));
+        return;
+    }
+    const int e0 = ph_begin(c);
+    norm_partial(w, ch, c->Pn, poison_ptr(c), c->stream);
+    ph_end(c, SVDSC_PH_VEC, e0, 1, 8.0 * ch.len, 2.0 * ch.len);
+    const int e1 = ph_begin(c);
+    const double L = (double)ch.len, w1 = W32 ? 4.0 : 8.0;
+    pr_omega(side, ncols, c->pr_kk, c->T, c->t + 1, c->mu, c->nu, ch, c->Pn, c->st, c->parity, c->pr,
+             (w1 + 8.0) * L * ncols + 16.0 * L, (w1 + 8.0) * L * ncols + 32.0 * L, 4.0 * L * ncols,
+             c->stream);
+    ph_end(c, SVDSC_PH_OTHER, e1, 1, 0.0, 0.0);
+    cgs2(c, W, W32, ld, ncols, w, ch, &c->pr->gate, false);
+}
+
+// v_{i+1} = A^T u_i - alpha_i v_i, re-orthogonalized against v_1..v_i, beta_i = ||.||  (Alg. 1 lines 5-6)
 static int issue_v(svdsc_ctx *c, int i)
 {
     double *out = colV(c, i);
     int rc = apply_A(c, 1, colU(c, i - 1), colU32(c, i - 1), colV(c, i - 1), Tent(c, i - 1, i - 1), 0.0,
                      out, poison_ptr(c));
     if (rc) return rc;
-    cgs2(c, c->V, c->V32, c->ldv, i, out, c->cn, poison_ptr(c));
+    reorth_vector(c, 1, i, out);
     do_finalize(c, 1, i, Tent(c, i - 1, i), 0);
     return SVDSC_OK;
 }
 
-// u_{i+1} = A v_{i+1} - beta_i u_i, CGS2 against u_1..u_i, alpha_{i+1}  (Alg. 1 lines 7-8)
+// u_{i+1} = A v_{i+1} - beta_i u_i, re-orthogonalized against u_1..u_i, alpha_{i+1}  (Alg. 1 lines 7-8)
 static int issue_u(svdsc_ctx *c, int i)
 {
     double *out = colU(c, i);
     int rc = apply_A(c, 0, colV(c, i), colV32(c, i), colU(c, i - 1), Tent(c, i - 1, i), 0.0, out,
                      poison_ptr(c));
     if (rc) return rc;
-    cgs2(c, c->U, c->U32, c->ldu, i, out, c->cm, poison_ptr(c));
+    reorth_vector(c, 0, i, out);
     do_finalize(c, 0, i, Tent(c, i, i), 0);
     return SVDSC_OK;
 }
@@ -579,6 +615,10 @@ static int settle(svdsc_ctx *c)
             if (rec.side == 0) Te = Tent(c, rec.col, rec.col);
             else Te = Tent(c, rec.col - 1, rec.col);
             do_finalize(c, rec.side, rec.col, Te, 2);
+            if (c->reorth) {  // the repaired vector is orthogonal to its predecessors
+                pr_reset(rec.side, rec.col, c->mu, c->nu, c->pr, c->stream);
+                ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0);
+            }
             rc = read_status(c);
             if (rc) return rc;
             repaired = !c->st_host->poison;
@@ -661,6 +701,8 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
     c->which = opt ? opt->which : SVDSC_LARGEST;
     if ((c->which != SVDSC_LARGEST && c->which != SVDSC_SMALLEST) ||
         (c->which == SVDSC_SMALLEST && A->m < A->n)) { delete c; return SVDSC_ERR_ARG; }
+    c->reorth = opt ? opt->reorth : SVDSC_REORTH_FULL;
+    if (c->reorth != SVDSC_REORTH_FULL && c->reorth != SVDSC_REORTH_PARTIAL) { delete c; return SVDSC_ERR_ARG; }
     c->format = A->format;
     c->m = A->m;
     c->n = A->n;
@@ -745,6 +787,8 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     c->n_steps = 0;
     c->steps.clear();
     c->steps.reserve(4 * (size_t)t);
+    c->pr_kk = 0;
+    if (c->reorth) pr_reset(0, -1, c->mu, c->nu, c->pr, s);  // nu_1 = mu_1 = 1, counters cleared
     {
         DevStatus init;
         memset(&init, 0, sizeof(init));
@@ -847,6 +891,11 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         }
         restart_T_kernel<<<1, 256, 0, s>>>(t, k, c->T, c->Sh, c->rho);
         ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0);
+        if (c->reorth) {
+            pr_restart(t, k, c->Vh, c->mu, c->nu, c->pr, s);
+            ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0);
+            c->pr_kk = k;
+        }
         CU(cudaGetLastError());
         // u_{k+1} = A v_{k+1} - U~_k rho (Eq. 7), re-orthogonalized against U~_k
         rc = apply_A(c, 0, colV(c, k), colV32(c, k), nullptr, nullptr, 0.0, colU(c, k), poison_ptr(c));
@@ -910,6 +959,18 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
             info->launches[i] = c->ph_launch[i];
             info->bytes[i] = c->ph_bytes[i];
             info->flops[i] = c->ph_flops[i];
+        }
+        // every Lanczos vector but u_1 (full), or the estimate-driven ones plus
+        // the restart vectors (partial), whose CGS2 bytes were counted on the device
+        info->n_reorth = c->n_steps - 1;
+        if (c->reorth) {
+            PrState ps;
+            CU(cudaMemcpy(&ps, c->pr, sizeof(PrState), cudaMemcpyDeviceToHost));
+            info->n_reorth = ps.n_reorth + restarts;
+            info->bytes[SVDSC_PH_GEMV_T] += ps.bytes_t;
+            info->bytes[SVDSC_PH_GEMV_N] += ps.bytes_n;
+            info->flops[SVDSC_PH_GEMV_T] += ps.flops;
+            info->flops[SVDSC_PH_GEMV_N] += ps.flops;
         }
         for (const auto &r : c->recs) {
             float ms = 0.f;
