@@ -162,8 +162,10 @@ __host__ __device__ __forceinline__ int core_off(int row, int kk, int rows)
 }
 
 // ------------------------------------------------------------ slicing
-// FP64 form: x = sum_{s=1..9} digit_s 2^(e - 6 s), digits signed with |digit| <= 63,
-// e = the row (or column) exponent with max |x| < 2^e.
+// FP64 form: x = sum_{s=0..7} d_s 2^(e - 5 - 7 s) up to a truncation below
+// 2^(e - 54), with balanced base-128 digits d_s in [-64, 63] and e the row (or
+// column) exponent with max |x| < 2^e.  (Eight balanced digits reach
+// 63 (128^8 - 1) / 127 ~ 0.99 * 2^55; the fixed-point value stays below 2^54.)
 __device__ __forceinline__ int dexp_of(double v)
 {
     const uint64_t b = (uint64_t)__double_as_longlong(v);
@@ -171,19 +173,31 @@ __device__ __forceinline__ int dexp_of(double v)
     return E == 0 ? -100000 : E - 1022;  // |v| < 2^(E-1022); zero/denormal ignored
 }
 
-__device__ __forceinline__ void ozaki_digits(double v, int e, float (&dig)[9])
+constexpr int kDigits = 8;
+// 64 * sum_{s<8} 128^s: adding it makes every base-128 digit of F + bias equal
+// d_s + 64 (in [0, 127]) for the balanced digits d_s of F, |F| < 2^54
+constexpr int64_t kDigitBias = 64ll * (((1ll << 56) - 1) / 127);
+
+// The FP32 bit patterns of d_s (their high halves are the exact BF16 values:
+// |d_s| <= 64 has at most 7 significant bits).  Integer ops and one FP32 add
+// per digit, no conversion instructions: float(2^23 + u) - (2^23 + 64) = u - 64.
+__device__ __forceinline__ void ozaki_digits(double v, int e, uint32_t (&bits)[kDigits])
 {
     const uint64_t b = (uint64_t)__double_as_longlong(v);
     const int E = (int)((b >> 52) & 0x7FF);
-    const float sg = (b >> 63) ? -1.f : 1.f;
-    uint64_t F = 0;
+    int64_t F = 0;
     if (E != 0) {
         const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = e - (E - 1022);   // >= 0
-        F = sh >= 54 ? 0ull : ((mant << 1) >> sh);  // |v| 2^(54 - e), < 2^54
+        const int sh = e - (E - 1022);   // >= 0 since |v| < 2^e
+        F = sh >= 54 ? 0 : (int64_t)((mant << 1) >> sh);  // |v| 2^(54 - e), < 2^54
+        if (b >> 63) F = -F;
     }
+    const uint64_t G = (uint64_t)(F + kDigitBias);
 #pragma unroll
-    for (int s = 0; s < 9; s++) dig[s] = sg * (float)(int)((F >> (6 * (8 - s))) & 63u);
+    for (int s = 0; s < kDigits; s++) {
+        const uint32_t u = (uint32_t)(G >> (7 * (kDigits - 1 - s))) & 127u;
+        bits[s] = __float_as_uint(__uint_as_float(0x4B000000u | u) - 8388672.0f);
+    }
 }
 
 // mixed form: x = hi + mid + lo, each a BF16 number (24 significant bits)
@@ -224,37 +238,39 @@ __global__ void prep_b_kernel(const double *__restrict__ Q, int64_t ldq, int t, 
     for (int kk = 0; kk < kKC; kk++) {
         const int c = chunk * kKC + kk;
         const double q = (j < k && c < t) ? Q[c + (int64_t)j * ldq] : 0.0;
-        float pieces[S];
+        uint16_t pieces[S];
         if constexpr (OZAKI) {
-            float d9[9];
-            ozaki_digits(q, e, d9);
+            uint32_t d[kDigits];
+            ozaki_digits(q, e, d);
 #pragma unroll
-            for (int s = 0; s < S; s++) pieces[s] = d9[s];
+            for (int s = 0; s < S; s++) pieces[s] = (uint16_t)(d[s] >> 16);
         } else {
             float p3[3];
             float_pieces((float)q, p3);
 #pragma unroll
-            for (int s = 0; s < S; s++) pieces[s] = p3[s];
+            for (int s = 0; s < S; s++) pieces[s] = __bfloat16_as_ushort(__float2bfloat16_rn(p3[s]));
         }
 #pragma unroll
         for (int s = 0; s < S; s++) {
             uint16_t *dst = Bs + ((int64_t)(cb * nchunks + chunk) * S + s) * (NT * kKC);
-            dst[core_off(jn, kk, NT) / 2] = __bfloat16_as_ushort(__float2bfloat16_rn(pieces[s]));
+            dst[core_off(jn, kk, NT) / 2] = pieces[s];
         }
     }
 }
 
 // ------------------------------------------------------------- main kernel
-// G accumulators of NT columns: OZAKI -> one per digit weight d = s+s' (G = 9),
-// else a single one.  C = W Q for rows [128 bx, +128) and columns [NT by, +NT).
+// G accumulators of NT columns: OZAKI -> one per digit weight g = s + s' <= 7
+// (G = 8, 36 digit products), else a single one.  C = W Q for rows
+// [128 tile, +128) and columns [NT cb, +NT).
 template <int S, int NT, bool OZAKI, typename WT>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k,
                const uint16_t *__restrict__ Bs, const int *__restrict__ fexp, int nchunks, int ncb,
                double *__restrict__ C, int64_t ldc, float *__restrict__ C32, int *err)
 {
-    constexpr int G = OZAKI ? 10 : 1;           // accumulators
-    constexpr int kMaxSum = OZAKI ? 9 : S - 1;  // kept pairs: s + s2 <= kMaxSum (0-based)
+    constexpr int G = OZAKI ? 8 : 1;            // accumulators
+    constexpr int kMaxSum = OZAKI ? 7 : S - 1;  // kept pairs: s + s2 <= kMaxSum (0-based)
+    static_assert(!OZAKI || S == kDigits, "digit count");
     constexpr uint32_t kTmemCols = (G * NT <= 32) ? 32 : (G * NT <= 64) ? 64 : (G * NT <= 128) ? 128
                                    : (G * NT <= 256) ? 256 : 512;
     static_assert(G * NT <= 512, "TMEM capacity");
@@ -324,32 +340,44 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
 #pragma unroll
         for (int kh = 0; kh < kKC / 16; kh++) {
             const int kg = half * (kKC / 16) + kh;
-            float pc[S][8];
+            double vals[8];
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
+            for (int q = 0; q < 8; q++) {  // all loads first
                 const int c = chunk * kKC + kg * 8 + q;
-                const double v = (row_ok && c < t) ? (double)W[r + (int64_t)c * ldw] : 0.0;
-                if constexpr (OZAKI) {
-                    float d9[9];
-                    ozaki_digits(v, e_r, d9);
+                vals[q] = (row_ok && c < t) ? (double)W[r + (int64_t)c * ldw] : 0.0;
+            }
+            const int off = core_off(trow, kg * 8, kTM);
+            if constexpr (OZAKI) {
+                uint32_t pc[8][kDigits];
 #pragma unroll
-                    for (int s = 0; s < S; s++) pc[s][q] = d9[s];
-                } else {
+                for (int q = 0; q < 8; q++) ozaki_digits(vals[q], e_r, pc[q]);
+#pragma unroll
+                for (int s = 0; s < S; s++) {
+                    uint4 w4;  // BF16 = high half of each FP32 pattern; two per word
+                    w4.x = __byte_perm(pc[0][s], pc[1][s], 0x7632);
+                    w4.y = __byte_perm(pc[2][s], pc[3][s], 0x7632);
+                    w4.z = __byte_perm(pc[4][s], pc[5][s], 0x7632);
+                    w4.w = __byte_perm(pc[6][s], pc[7][s], 0x7632);
+                    *(uint4 *)(A + s * Cfg::a_slice_bytes + off) = w4;
+                }
+            } else {
+                float pc[S][8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
                     float p3[3];
-                    float_pieces((float)v, p3);
+                    float_pieces((float)vals[q], p3);
 #pragma unroll
                     for (int s = 0; s < S; s++) pc[s][q] = p3[s];
                 }
-            }
-            const int off = core_off(trow, kg * 8, kTM);
 #pragma unroll
-            for (int s = 0; s < S; s++) {
-                uint4 w4;
-                w4.x = pack_bf16(pc[s][0], pc[s][1]);
-                w4.y = pack_bf16(pc[s][2], pc[s][3]);
-                w4.z = pack_bf16(pc[s][4], pc[s][5]);
-                w4.w = pack_bf16(pc[s][6], pc[s][7]);
-                *(uint4 *)(A + s * Cfg::a_slice_bytes + off) = w4;
+                for (int s = 0; s < S; s++) {
+                    uint4 w4;
+                    w4.x = pack_bf16(pc[s][0], pc[s][1]);
+                    w4.y = pack_bf16(pc[s][2], pc[s][3]);
+                    w4.z = pack_bf16(pc[s][4], pc[s][5]);
+                    w4.w = pack_bf16(pc[s][6], pc[s][7]);
+                    *(uint4 *)(A + s * Cfg::a_slice_bytes + off) = w4;
+                }
             }
         }
         fence_proxy_async_smem();
@@ -402,11 +430,13 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
             if (j0 + c8 >= k) break;
             double out[8];
             if constexpr (OZAKI) {
-                // X_d (d = g + 2) are exact integers; Horner in three exact
-                // int64 groups: d = 2..5, 6..8, 9..11
-                long long zh[8], zm[8], zl[8];
+                // X_g = sum over K and s + s' = g of d_s d'_s' are exact integers
+                // (|X_g| <= 8 * 448 * 64^2 < 2^24); the product is
+                // sum_g X_g 2^(e_r + e_j - 10 - 7 g).  Horner in two exact int64
+                // groups (|z| < 2^46): g = 0..3 and 4..7, then one FP64 rounding.
+                long long zh[8], zl[8];
 #pragma unroll
-                for (int q = 0; q < 8; q++) { zh[q] = 0; zm[q] = 0; zl[q] = 0; }
+                for (int q = 0; q < 8; q++) { zh[q] = 0; zl[q] = 0; }
 #pragma unroll
                 for (int g = 0; g < G; g++) {
                     uint32_t x[8];
@@ -414,16 +444,15 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
 #pragma unroll
                     for (int q = 0; q < 8; q++) {
                         const long long xi = (long long)__float2int_rn(__uint_as_float(x[q]));
-                        if (g < 4) zh[q] = zh[q] * 64 + xi;
-                        else if (g < 7) zm[q] = zm[q] * 64 + xi;
-                        else zl[q] = zl[q] * 64 + xi;
+                        if (g < 4) zh[q] = zh[q] * 128 + xi;
+                        else zl[q] = zl[q] * 128 + xi;
                     }
                 }
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
                     const int j = j0 + c8 + q;
                     const int ef = (j < k) ? fexp[j] : 0;
-                    const double v = fma((double)zh[q], 0x1p-30, fma((double)zm[q], 0x1p-48, (double)zl[q] * 0x1p-66));
+                    const double v = fma((double)zh[q], 0x1p-31, (double)zl[q] * 0x1p-59);
                     out[q] = (e_r < -99999 || ef < -99999) ? 0.0 : ldexp(v, e_r + ef);
                 }
             } else {
@@ -461,7 +490,7 @@ static size_t bs_bytes(int t, int k)
 
 static size_t slices_bytes(int t, int k)
 {
-    size_t a = bs_bytes<9, 48, true>(t, k);  // 10 x 48 = 480 TMEM columns
+    size_t a = bs_bytes<kDigits, 64, true>(t, k);  // 8 x 64 = 512 TMEM columns
     size_t b = bs_bytes<3, 128, false>(t, k);
     return ((a > b ? a : b) + 255) & ~(size_t)255;
 }
@@ -503,7 +532,8 @@ cudaError_t tc_gemm(int mode, const double *W, const float *W32, int64_t ldw, in
     uint16_t *bs = (uint16_t *)ws;
     int *fx = (int *)((uint8_t *)ws + slices_bytes(t, k));
     if (launches) *launches += 2;
-    if (mode == 0) return launch_tc<9, 48, true, double>(W, ldw, rows, t, Q, ldq, k, C, ldc, C32, bs, fx, err, s);
+    if (mode == 0)
+        return launch_tc<kDigits, 64, true, double>(W, ldw, rows, t, Q, ldq, k, C, ldc, C32, bs, fx, err, s);
     if (W32) return launch_tc<3, 128, false, float>(W32, ldw, rows, t, Q, ldq, k, C, ldc, C32, bs, fx, err, s);
     return launch_tc<3, 128, false, double>(W, ldw, rows, t, Q, ldq, k, C, ldc, C32, bs, fx, err, s);
 }
