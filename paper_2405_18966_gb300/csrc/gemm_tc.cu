@@ -2,17 +2,21 @@
 // paper): C (rows x k) = W (rows x t) Q (t x k), W tall and skinny, on the
 // 5th-generation tensor cores (tcgen05.mma, accumulators in TMEM).
 //
-// Operands are cut into BF16 "slices" and every slice pair with s + s' <= S + 1
-// is multiplied on the tensor cores with FP32 accumulation:
+// Operands are cut into BF16 "slices" and the slice pairs that matter are
+// multiplied on the tensor cores with FP32 accumulation:
 //   * FP64 form (Ozaki-style error-free splitting, Ozaki et al. 2012): each row
 //     of W and each column of Q is scaled by a power of two, its fixed-point
-//     value is cut into S = 9 signed 6-bit digits (54 bits), and the 53 digit
-//     products with s + s' <= 11 are summed in 10 TMEM accumulators, one per
-//     digit weight d = s + s'.  Every accumulator holds an integer below 2^24
-//     (t <= 448), so the FP32 tensor-core sums are exact; the epilogue
-//     recombines the 10 integers exactly in int64 and rounds once to FP64.
-//     The dropped products (s + s' >= 12) bound the error by about
-//     2^-49 max|W(r,:)| max|Q(:,j)| (worst case; typically 2^-55).
+//     value (54 bits) is cut into S = 8 balanced base-128 digits in [-64, 63],
+//     built directly as BF16 bit patterns, and the 36 digit products with
+//     s + s' <= 7 are summed in 8 TMEM accumulators, one per digit weight
+//     g = s + s'.  Every accumulator holds an integer below 8 * 448 * 64^2 <
+//     2^24 (t <= 448), so the FP32 tensor-core sums are exact; the epilogue
+//     recombines the 8 integers exactly in two int64 groups and rounds once to
+//     FP64.  The dropped products (s + s' >= 8) and the truncation below
+//     2^-54 of each row's or column's scale bound the error by about
+//     2^-49 max|W(r,:)| max|Q(:,j)| per term of the K sum in the worst case
+//     (random signs: far less; inside 8 eps sum |W||Q| + 2^-47 max max in the
+//     parity tests).
 //   * mixed form: W (FP32 shadow) and Q are cut into 3 floating BF16 pieces
 //     (hi, mid, lo: 24 bits) and the 6 products with s + s' <= 4 accumulate in
 //     one FP32 accumulator.
