@@ -204,6 +204,37 @@ __device__ __forceinline__ void ozaki_digits(double v, int e, uint32_t (&bits)[k
     }
 }
 
+// round(Z 2^(E - 59)) for the exact integer Z = zh 2^28 + zl (|zh|, |zl| < 2^46),
+// to nearest even, assembled from integer ops (the FP64 pipe is GB300's
+// scarcest); false when the result is not a normal FP64 number.
+__device__ __forceinline__ bool compose_f64(long long zh, long long zl, int E, double &out)
+{
+    const __int128 Z = ((__int128)zh << 28) + (__int128)zl;
+    if (Z == 0) { out = 0.0; return true; }
+    const bool neg = Z < 0;
+    const unsigned __int128 M = neg ? (unsigned __int128)(-Z) : (unsigned __int128)Z;
+    const uint64_t hi = (uint64_t)(M >> 64), lo = (uint64_t)M;
+    const int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading bit
+    int ex = p + E - 59 + 1023;
+    uint64_t mant;
+    if (p <= 52) {
+        mant = lo << (52 - p);
+    } else {
+        const int sh = p - 52;  // 1 .. 75
+        mant = (uint64_t)(M >> sh);
+        const unsigned __int128 rem = M & (((unsigned __int128)1 << sh) - 1);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) {
+            mant++;
+            if (mant >> 53) { mant >>= 1; ex++; }
+        }
+    }
+    if (ex <= 0 || ex >= 2047) return false;
+    out = __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)ex << 52) |
+                                           (mant & ((1ull << 52) - 1))));
+    return true;
+}
+
 // mixed form: x = hi + mid + lo, each a BF16 number (24 significant bits)
 __device__ __forceinline__ void float_pieces(float x, float (&p)[3])
 {
@@ -325,7 +356,21 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
     uint32_t parity[2] = {0u, 0u};
     bool used[2] = {false, false};
     bool ok = true;
+    // this thread's W entries of a chunk: its row, K groups kg = 2 half + kh;
+    // the next chunk's are loaded while the current one is cut
+    double cur[kKC / 16][8], nxt[kKC / 16][8];
+    auto load_chunk = [&](int chunk, double (&dst)[kKC / 16][8]) {
+#pragma unroll
+        for (int kh = 0; kh < kKC / 16; kh++)
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int c = chunk * kKC + (half * (kKC / 16) + kh) * 8 + q;
+                dst[kh][q] = (row_ok && c < t) ? (double)W[r + (int64_t)c * ldw] : 0.0;
+            }
+    };
+    load_chunk(0, cur);
     for (int chunk = 0; chunk < nchunks; chunk++) {
+        if (chunk + 1 < nchunks) load_chunk(chunk + 1, nxt);
         const int st = chunk & 1;
         uint8_t *A = smem + st * Cfg::stage_bytes;
         uint8_t *B = A + Cfg::a_bytes;
@@ -344,12 +389,7 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
 #pragma unroll
         for (int kh = 0; kh < kKC / 16; kh++) {
             const int kg = half * (kKC / 16) + kh;
-            double vals[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) {  // all loads first
-                const int c = chunk * kKC + kg * 8 + q;
-                vals[q] = (row_ok && c < t) ? (double)W[r + (int64_t)c * ldw] : 0.0;
-            }
+            const double *vals = cur[kh];
             const int off = core_off(trow, kg * 8, kTM);
             if constexpr (OZAKI) {
                 uint32_t pc[8][kDigits];
@@ -414,6 +454,10 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
             umma_commit(&mma_done[st]);
         }
         used[st] = true;
+#pragma unroll
+        for (int kh = 0; kh < kKC / 16; kh++)
+#pragma unroll
+            for (int q = 0; q < 8; q++) cur[kh][q] = nxt[kh][q];
     }
     // wait for the last commits of both stages
     for (int st = 0; st < 2; st++)
@@ -456,8 +500,10 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
                 for (int q = 0; q < 8; q++) {
                     const int j = j0 + c8 + q;
                     const int ef = (j < k) ? fexp[j] : 0;
-                    const double v = fma((double)zh[q], 0x1p-31, (double)zl[q] * 0x1p-59);
-                    out[q] = (e_r < -99999 || ef < -99999) ? 0.0 : ldexp(v, e_r + ef);
+                    double o = 0.0;
+                    if (e_r > -99999 && ef > -99999 && !compose_f64(zh[q], zl[q], e_r + ef, o))
+                        o = ldexp(fma((double)zh[q], 0x1p-31, (double)zl[q] * 0x1p-59), e_r + ef);
+                    out[q] = o;
                 }
             } else {
                 uint32_t x[8];
