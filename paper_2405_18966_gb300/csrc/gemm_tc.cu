@@ -65,6 +65,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared on the TMA engine; completion counted in bytes
+// on `bar` (dst, src 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void fence_barrier_init()
 {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -145,7 +160,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 // ------------------------------------------------------------- geometry
 constexpr int kTM = 128;        // rows per CTA (MMA M)
 constexpr int kKC = 32;         // K chunk per pipeline stage
-constexpr int kThreads = 256;   // two threads per row of the tile (each cuts half of a chunk)
+constexpr int kThreads = 512;   // four threads per row of the tile
+constexpr int kTPR = kThreads / kTM;         // threads per row
+constexpr int kGPT = (kKC / 8) / kTPR;       // groups of 8 K entries each thread cuts per chunk
+static_assert(kGPT >= 1 && kGPT * kTPR * 8 == kKC, "chunk split");
 constexpr int kMaxT = 448;      // exactness bound of the FP64 form
 
 template <int S, int NT>
@@ -312,12 +330,12 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
     using Cfg = TileCfg<S, NT>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t mma_done[2];
+    __shared__ uint64_t mma_done[2], b_full[2];
     __shared__ uint32_t tmem_base_slot;
     __shared__ int s_er[kTM];
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int trow = tid & (kTM - 1), half = tid >> 7;
+    const int trow = tid & (kTM - 1), part = tid >> 7;  // part in [0, kTPR)
     // the column blocks of one row tile are adjacent in launch order, so the
     // tile's rows of W are re-read from L2 rather than DRAM
     const int64_t tile = (int64_t)blockIdx.x / ncb;
@@ -329,6 +347,8 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
     if (tid == 0) {
         mbar_init(&mma_done[0], 1);
         mbar_init(&mma_done[1], 1);
+        mbar_init(&b_full[0], 1);
+        mbar_init(&b_full[1], 1);
         fence_barrier_init();
     }
     if (warp == 0) {
@@ -340,31 +360,31 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
     tc_fence_after();
     const uint32_t tmem = tmem_base_slot;
 
-    // row exponent (FP64 form): each half scans half of the columns
+    // row exponent (FP64 form): each part scans every kTPR-th column
     int e_r = -100000;
     if (OZAKI) {
         int e_h = -100000;
         if (row_ok)
-            for (int c = half; c < t; c += 2) e_h = max(e_h, dexp_of((double)W[r + (int64_t)c * ldw]));
-        if (half == 1) s_er[trow] = e_h;
+            for (int c = part; c < t; c += kTPR) e_h = max(e_h, dexp_of((double)W[r + (int64_t)c * ldw]));
+        if (part == 0) s_er[trow] = -100000;
         __syncthreads();
-        if (half == 0) s_er[trow] = max(e_h, s_er[trow]);
+        atomicMax(&s_er[trow], e_h);
         __syncthreads();
         e_r = s_er[trow];
     }
 
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t parity[2] = {0u, 0u}, bpar[2] = {0u, 0u};
     bool used[2] = {false, false};
     bool ok = true;
-    // this thread's W entries of a chunk: its row, K groups kg = 2 half + kh;
+    // this thread's W entries of a chunk: its row, K groups kg = kGPT part + kh;
     // the next chunk's are loaded while the current one is cut
-    double cur[kKC / 16][8], nxt[kKC / 16][8];
-    auto load_chunk = [&](int chunk, double (&dst)[kKC / 16][8]) {
+    double cur[kGPT][8], nxt[kGPT][8];
+    auto load_chunk = [&](int chunk, double (&dst)[kGPT][8]) {
 #pragma unroll
-        for (int kh = 0; kh < kKC / 16; kh++)
+        for (int kh = 0; kh < kGPT; kh++)
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-                const int c = chunk * kKC + (half * (kKC / 16) + kh) * 8 + q;
+                const int c = chunk * kKC + (part * kGPT + kh) * 8 + q;
                 dst[kh][q] = (row_ok && c < t) ? (double)W[r + (int64_t)c * ldw] : 0.0;
             }
     };
@@ -379,16 +399,17 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
             parity[st] ^= 1u;
         }
         tc_fence_after();
-        // B slices for (cb, chunk): contiguous, copied as 16-byte words
-        {
-            const uint4 *src = (const uint4 *)(Bs + (int64_t)(cb * nchunks + chunk) * S * (NT * kKC));
-            uint4 *dst = (uint4 *)B;
-            for (int i = tid; i < Cfg::b_bytes / 16; i += kThreads) dst[i] = src[i];
+        // B slices for (cb, chunk): one contiguous bulk copy, in flight while
+        // the threads cut the A slices
+        if (tid == 0) {
+            mbar_expect_tx(&b_full[st], (uint32_t)Cfg::b_bytes);
+            bulk_g2s(B, Bs + (int64_t)(cb * nchunks + chunk) * S * (NT * kKC), (uint32_t)Cfg::b_bytes,
+                     &b_full[st]);
         }
-        // A slices: this thread's row, its half of the 4 groups of 8 consecutive K entries
+        // A slices: this thread's row, its kGPT of the 4 groups of 8 consecutive K entries
 #pragma unroll
-        for (int kh = 0; kh < kKC / 16; kh++) {
-            const int kg = half * (kKC / 16) + kh;
+        for (int kh = 0; kh < kGPT; kh++) {
+            const int kg = part * kGPT + kh;
             const double *vals = cur[kh];
             const int off = core_off(trow, kg * 8, kTM);
             if constexpr (OZAKI) {
@@ -429,6 +450,10 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
+            if (!mbar_wait_bounded(&b_full[st], bpar[st])) ok = false;
+            bpar[st] ^= 1u;
+        }
+        if (tid == 0 && ok) {
             constexpr uint32_t idesc = idesc_bf16(kTM, NT);
             const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
             constexpr uint32_t a_lbo = (kTM / 8) * 128, a_sbo = 128;
@@ -451,11 +476,13 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
                     }
                 }
             }
-            umma_commit(&mma_done[st]);
         }
+        // (after a failed wait the commit arrives with no MMAs: the stage is
+        // released and the error surfaces through `ok`)
+        if (tid == 0) umma_commit(&mma_done[st]);
         used[st] = true;
 #pragma unroll
-        for (int kh = 0; kh < kKC / 16; kh++)
+        for (int kh = 0; kh < kGPT; kh++)
 #pragma unroll
             for (int q = 0; q < 8; q++) cur[kh][q] = nxt[kh][q];
     }
@@ -471,10 +498,10 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
         if (tid == 0) atomicExch(err, 1);
     } else {
         // epilogue: warp w reads TMEM lanes 32(w mod 4).. = rows 32(w mod 4)..;
-        // the two halves take alternate groups of 8 columns
+        // the kTPR parts of a row take interleaved groups of 8 columns
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const int j0 = cb * NT;
-        for (int c8 = half * 8; c8 < NT; c8 += 16) {
+        for (int c8 = part * 8; c8 < NT; c8 += 8 * kTPR) {
             if (j0 + c8 >= k) break;
             double out[8];
             if constexpr (OZAKI) {
