@@ -65,6 +65,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -160,8 +165,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 // ------------------------------------------------------------- geometry
 constexpr int kTM = 128;        // rows per CTA (MMA M)
 constexpr int kKC = 32;         // K chunk per pipeline stage
-constexpr int kThreads = 512;   // four threads per row of the tile
-constexpr int kTPR = kThreads / kTM;         // threads per row
+constexpr int kCutThreads = 512;             // cutters: four threads per row of the tile
+constexpr int kThreads = kCutThreads + 32;   // + one warp that issues the MMAs
+constexpr int kTPR = kCutThreads / kTM;      // threads per row
 constexpr int kGPT = (kKC / 8) / kTPR;       // groups of 8 K entries each thread cuts per chunk
 static_assert(kGPT >= 1 && kGPT * kTPR * 8 == kKC, "chunk split");
 constexpr int kMaxT = 448;      // exactness bound of the FP64 form
@@ -330,25 +336,29 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
     using Cfg = TileCfg<S, NT>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t mma_done[2], b_full[2];
+    // per stage: A slices written (one arrival per cutter warp), B slices
+    // landed (bulk copy bytes), MMAs that read the stage done (tcgen05.commit)
+    __shared__ uint64_t a_full[2], b_full[2], mma_done[2];
     __shared__ uint32_t tmem_base_slot;
     __shared__ int s_er[kTM];
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int trow = tid & (kTM - 1), part = tid >> 7;  // part in [0, kTPR)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool cutter = tid < kCutThreads;
+    const int trow = tid & (kTM - 1), part = tid >> 7;  // cutters: part in [0, kTPR)
     // the column blocks of one row tile are adjacent in launch order, so the
     // tile's rows of W are re-read from L2 rather than DRAM
     const int64_t tile = (int64_t)blockIdx.x / ncb;
     const int cb = (int)(blockIdx.x % ncb);
     const int64_t row0 = tile * kTM;
     const int64_t r = row0 + trow;
-    const bool row_ok = r < rows;
+    const bool row_ok = cutter && r < rows;
 
     if (tid == 0) {
-        mbar_init(&mma_done[0], 1);
-        mbar_init(&mma_done[1], 1);
-        mbar_init(&b_full[0], 1);
-        mbar_init(&b_full[1], 1);
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&a_full[i], kCutThreads / 32);
+            mbar_init(&b_full[i], 1);
+            mbar_init(&mma_done[i], 1);
+        }
         fence_barrier_init();
     }
     if (warp == 0) {
@@ -366,137 +376,155 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
         int e_h = -100000;
         if (row_ok)
             for (int c = part; c < t; c += kTPR) e_h = max(e_h, dexp_of((double)W[r + (int64_t)c * ldw]));
-        if (part == 0) s_er[trow] = -100000;
+        if (cutter && part == 0) s_er[trow] = -100000;
         __syncthreads();
-        atomicMax(&s_er[trow], e_h);
+        if (cutter) atomicMax(&s_er[trow], e_h);
         __syncthreads();
-        e_r = s_er[trow];
+        e_r = cutter ? s_er[trow] : 0;
     }
 
-    uint32_t parity[2] = {0u, 0u}, bpar[2] = {0u, 0u};
+    uint32_t parity[2] = {0u, 0u};
     bool used[2] = {false, false};
     bool ok = true;
-    // this thread's W entries of a chunk: its row, K groups kg = kGPT part + kh;
-    // the next chunk's are loaded while the current one is cut
-    double cur[kGPT][8], nxt[kGPT][8];
-    auto load_chunk = [&](int chunk, double (&dst)[kGPT][8]) {
-#pragma unroll
-        for (int kh = 0; kh < kGPT; kh++)
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const int c = chunk * kKC + (part * kGPT + kh) * 8 + q;
-                dst[kh][q] = (row_ok && c < t) ? (double)W[r + (int64_t)c * ldw] : 0.0;
-            }
-    };
-    load_chunk(0, cur);
-    for (int chunk = 0; chunk < nchunks; chunk++) {
-        if (chunk + 1 < nchunks) load_chunk(chunk + 1, nxt);
-        const int st = chunk & 1;
-        uint8_t *A = smem + st * Cfg::stage_bytes;
-        uint8_t *B = A + Cfg::a_bytes;
-        if (used[st]) {  // the MMAs that read this stage two chunks ago must be done
-            if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
-            parity[st] ^= 1u;
-        }
-        tc_fence_after();
-        // B slices for (cb, chunk): one contiguous bulk copy, in flight while
-        // the threads cut the A slices
-        if (tid == 0) {
-            mbar_expect_tx(&b_full[st], (uint32_t)Cfg::b_bytes);
-            bulk_g2s(B, Bs + (int64_t)(cb * nchunks + chunk) * S * (NT * kKC), (uint32_t)Cfg::b_bytes,
-                     &b_full[st]);
-        }
-        // A slices: this thread's row, its kGPT of the 4 groups of 8 consecutive K entries
-#pragma unroll
-        for (int kh = 0; kh < kGPT; kh++) {
-            const int kg = part * kGPT + kh;
-            const double *vals = cur[kh];
-            const int off = core_off(trow, kg * 8, kTM);
-            if constexpr (OZAKI) {
-                uint32_t pc[8][kDigits];
-#pragma unroll
-                for (int q = 0; q < 8; q++) ozaki_digits(vals[q], e_r, pc[q]);
-#pragma unroll
-                for (int s = 0; s < S; s++) {
-                    uint4 w4;  // BF16 = high half of each FP32 pattern; two per word
-                    w4.x = __byte_perm(pc[0][s], pc[1][s], 0x7632);
-                    w4.y = __byte_perm(pc[2][s], pc[3][s], 0x7632);
-                    w4.z = __byte_perm(pc[4][s], pc[5][s], 0x7632);
-                    w4.w = __byte_perm(pc[6][s], pc[7][s], 0x7632);
-                    *(uint4 *)(A + s * Cfg::a_slice_bytes + off) = w4;
+    if (!cutter) {
+        // MMA warp, one thread: stage free -> bulk copy of the B slices ->
+        // A slices written and B landed -> 36 (FP64) or 6 (mixed) products per
+        // 16-wide K step -> commit
+        if (lane == 0) {
+            uint32_t apar[2] = {0u, 0u}, bpar[2] = {0u, 0u};
+            for (int chunk = 0; chunk < nchunks; chunk++) {
+                const int st = chunk & 1;
+                uint8_t *A = smem + st * Cfg::stage_bytes;
+                uint8_t *B = A + Cfg::a_bytes;
+                if (used[st]) {
+                    if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
+                    parity[st] ^= 1u;
                 }
-            } else {
-                float pc[S][8];
+                mbar_expect_tx(&b_full[st], (uint32_t)Cfg::b_bytes);
+                bulk_g2s(B, Bs + (int64_t)(cb * nchunks + chunk) * S * (NT * kKC), (uint32_t)Cfg::b_bytes,
+                         &b_full[st]);
+                if (!mbar_wait_bounded(&a_full[st], apar[st])) ok = false;
+                apar[st] ^= 1u;
+                if (!mbar_wait_bounded(&b_full[st], bpar[st])) ok = false;
+                bpar[st] ^= 1u;
+                tc_fence_after();
+                if (ok) {
+                    constexpr uint32_t idesc = idesc_bf16(kTM, NT);
+                    const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+                    constexpr uint32_t a_lbo = (kTM / 8) * 128, a_sbo = 128;
+                    constexpr uint32_t b_lbo = (NT / 8) * 128, b_sbo = 128;
+#pragma unroll
+                    for (int ks = 0; ks < kKC / 16; ks++) {
+#pragma unroll
+                        for (int s = 0; s < S; s++) {
+#pragma unroll
+                            for (int s2 = 0; s2 < S; s2++) {
+                                if (s + s2 > kMaxSum) continue;
+                                const int g = OZAKI ? (s + s2) : 0;
+                                const uint64_t ad =
+                                    smem_desc(a0 + s * Cfg::a_slice_bytes + ks * 2 * a_lbo, a_lbo, a_sbo);
+                                const uint64_t bd =
+                                    smem_desc(b0 + s2 * Cfg::b_slice_bytes + ks * 2 * b_lbo, b_lbo, b_sbo);
+                                // the first product into each accumulator overwrites it:
+                                // group g = s + s2 is first reached at s = max(0, g - (S - 1))
+                                const int s_first = (OZAKI && g > S - 1) ? g - (S - 1) : 0;
+                                const bool first = chunk == 0 && ks == 0 && s == s_first && (OZAKI || s2 == 0);
+                                umma_bf16(tmem + (uint32_t)(g * NT), ad, bd, idesc, first ? 0u : 1u);
+                            }
+                        }
+                    }
+                }
+                // (after a failed wait the commit arrives with no MMAs: the
+                // stage is released and the error surfaces through `ok`)
+                umma_commit(&mma_done[st]);
+                used[st] = true;
+            }
+        }
+        __syncwarp();  // reconverge before the block-wide barrier
+    } else {
+        // cutters: this thread's W entries of a chunk are its row, K groups
+        // kg = kGPT part + kh; the next chunk's load while this one is cut
+        double cur[kGPT][8], nxt[kGPT][8];
+        auto load_chunk = [&](int chunk, double (&dst)[kGPT][8]) {
+#pragma unroll
+            for (int kh = 0; kh < kGPT; kh++)
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    float p3[3];
-                    float_pieces((float)vals[q], p3);
-#pragma unroll
-                    for (int s = 0; s < S; s++) pc[s][q] = p3[s];
+                    const int c = chunk * kKC + (part * kGPT + kh) * 8 + q;
+                    dst[kh][q] = (row_ok && c < t) ? (double)W[r + (int64_t)c * ldw] : 0.0;
                 }
-#pragma unroll
-                for (int s = 0; s < S; s++) {
-                    uint4 w4;
-                    w4.x = pack_bf16(pc[s][0], pc[s][1]);
-                    w4.y = pack_bf16(pc[s][2], pc[s][3]);
-                    w4.z = pack_bf16(pc[s][4], pc[s][5]);
-                    w4.w = pack_bf16(pc[s][6], pc[s][7]);
-                    *(uint4 *)(A + s * Cfg::a_slice_bytes + off) = w4;
-                }
+        };
+        load_chunk(0, cur);
+        for (int chunk = 0; chunk < nchunks; chunk++) {
+            if (chunk + 1 < nchunks) load_chunk(chunk + 1, nxt);
+            const int st = chunk & 1;
+            uint8_t *A = smem + st * Cfg::stage_bytes;
+            if (used[st]) {  // the MMAs that read this stage two chunks ago must be done
+                if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
+                parity[st] ^= 1u;
             }
-        }
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
             tc_fence_after();
-            if (!mbar_wait_bounded(&b_full[st], bpar[st])) ok = false;
-            bpar[st] ^= 1u;
-        }
-        if (tid == 0 && ok) {
-            constexpr uint32_t idesc = idesc_bf16(kTM, NT);
-            const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
-            constexpr uint32_t a_lbo = (kTM / 8) * 128, a_sbo = 128;
-            constexpr uint32_t b_lbo = (NT / 8) * 128, b_sbo = 128;
 #pragma unroll
-            for (int ks = 0; ks < kKC / 16; ks++) {
+            for (int kh = 0; kh < kGPT; kh++) {
+                const int kg = part * kGPT + kh;
+                const double *vals = cur[kh];
+                const int off = core_off(trow, kg * 8, kTM);
+                if constexpr (OZAKI) {
+                    uint32_t pc[8][kDigits];
 #pragma unroll
-                for (int s = 0; s < S; s++) {
+                    for (int q = 0; q < 8; q++) ozaki_digits(vals[q], e_r, pc[q]);
 #pragma unroll
-                    for (int s2 = 0; s2 < S; s2++) {
-                        if (s + s2 > kMaxSum) continue;
-                        const int g = OZAKI ? (s + s2) : 0;
-                        const uint64_t ad = smem_desc(a0 + s * Cfg::a_slice_bytes + ks * 2 * a_lbo, a_lbo, a_sbo);
-                        const uint64_t bd = smem_desc(b0 + s2 * Cfg::b_slice_bytes + ks * 2 * b_lbo, b_lbo, b_sbo);
-                        // the first product into each accumulator overwrites it:
-                        // group g = s + s2 is first reached at s = max(0, g - (S - 1))
-                        const int s_first = (OZAKI && g > S - 1) ? g - (S - 1) : 0;
-                        const bool first = chunk == 0 && ks == 0 && s == s_first && (OZAKI || s2 == 0);
-                        umma_bf16(tmem + (uint32_t)(g * NT), ad, bd, idesc, first ? 0u : 1u);
+                    for (int s = 0; s < S; s++) {
+                        uint4 w4;  // BF16 = high half of each FP32 pattern; two per word
+                        w4.x = __byte_perm(pc[0][s], pc[1][s], 0x7632);
+                        w4.y = __byte_perm(pc[2][s], pc[3][s], 0x7632);
+                        w4.z = __byte_perm(pc[4][s], pc[5][s], 0x7632);
+                        w4.w = __byte_perm(pc[6][s], pc[7][s], 0x7632);
+                        *(uint4 *)(A + s * Cfg::a_slice_bytes + off) = w4;
+                    }
+                } else {
+                    float pc[S][8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        float p3[3];
+                        float_pieces((float)vals[q], p3);
+#pragma unroll
+                        for (int s = 0; s < S; s++) pc[s][q] = p3[s];
+                    }
+#pragma unroll
+                    for (int s = 0; s < S; s++) {
+                        uint4 w4;
+                        w4.x = pack_bf16(pc[s][0], pc[s][1]);
+                        w4.y = pack_bf16(pc[s][2], pc[s][3]);
+                        w4.z = pack_bf16(pc[s][4], pc[s][5]);
+                        w4.w = pack_bf16(pc[s][6], pc[s][7]);
+                        *(uint4 *)(A + s * Cfg::a_slice_bytes + off) = w4;
                     }
                 }
             }
+            // generic-proxy writes -> visible to the tensor cores, then one
+            // arrival per warp
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[st]);
+            used[st] = true;
+#pragma unroll
+            for (int kh = 0; kh < kGPT; kh++)
+#pragma unroll
+                for (int q = 0; q < 8; q++) cur[kh][q] = nxt[kh][q];
         }
-        // (after a failed wait the commit arrives with no MMAs: the stage is
-        // released and the error surfaces through `ok`)
-        if (tid == 0) umma_commit(&mma_done[st]);
-        used[st] = true;
-#pragma unroll
-        for (int kh = 0; kh < kGPT; kh++)
-#pragma unroll
-            for (int q = 0; q < 8; q++) cur[kh][q] = nxt[kh][q];
+        // wait for the last commits of both stages
+        for (int st = 0; st < 2; st++)
+            if (used[st]) {
+                if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
+                parity[st] ^= 1u;
+            }
     }
-    // wait for the last commits of both stages
-    for (int st = 0; st < 2; st++)
-        if (used[st]) {
-            if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
-            parity[st] ^= 1u;
-        }
     tc_fence_after();
     ok = __syncthreads_and(ok) != 0;
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
-    } else {
+    } else if (cutter) {
         // epilogue: warp w reads TMEM lanes 32(w mod 4).. = rows 32(w mod 4)..;
         // the kTPR parts of a row take interleaved groups of 8 columns
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
