@@ -220,6 +220,18 @@ __device__ bool grid_sync(unsigned *bar, unsigned nblk, int *timeout)
     return s_ok != 0;
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ double block_sum_coop(double v, double *red, double *out)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -253,14 +265,40 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
     if (!grid_sync(bar, nblk, timeout)) return;
     const double tol = DBL_EPSILON * sqrt((double)t);
     const int n2 = t + (t & 1);
+    // Rounds are ordered by per-column version flags instead of grid
+    // barriers: flag[c] counts the rounds completed on column c, the CTA that
+    // owns the pair (p, q) in global round R waits (bounded) for both flags to
+    // reach R, rotates, and publishes R + 1.  Each column has exactly one
+    // reader-writer per round, so no other ordering is needed; one grid
+    // barrier per sweep remains for the convergence test.
+    unsigned *flag = bar + 2;
+    __shared__ int s_go;
+    unsigned R = 0;
     int sweeps = 0;
     bool conv = false;
     while (sweeps < max_sweeps) {
-        for (int round = 0; round < n2 - 1; round++) {
+        for (int round = 0; round < n2 - 1; round++, R++) {
             for (int slot = blockIdx.x; slot < n2 / 2; slot += nblk) {
                 int p, q;
                 rr_pair(slot, round, n2, &p, &q);
-                if (q >= t) continue;
+                const bool idle = q >= t;  // odd t: column p sits this round out
+                if (threadIdx.x == 0) {
+                    int ok = 1;
+                    unsigned long long spins = 0;
+                    while (ld_acquire_u32(flag + p) < R || (!idle && ld_acquire_u32(flag + q) < R)) {
+                        if (++spins > (1ull << 24) || *(volatile int *)timeout) { ok = 0; break; }
+                        if (spins > 256) __nanosleep(32);
+                    }
+                    if (!ok) atomicExch(timeout, 1);
+                    s_go = ok;
+                }
+                __syncthreads();
+                if (!s_go) return;
+                if (idle) {
+                    if (threadIdx.x == 0) st_release_u32(flag + p, R + 1);
+                    __syncthreads();  // s_go is read by every thread before thread 0 rewrites it
+                    continue;
+                }
                 double *bp = B + (int64_t)p * t, *bq = B + (int64_t)q * t;
                 double *wp = W + (int64_t)p * t, *wq = W + (int64_t)q * t;
                 // every element of both pairs of columns is loaded once, up front
@@ -301,21 +339,28 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
                 double c, s;
                 const bool do_rot = jacobi_rotation(sv[0], sv[1], sv[2], tol, &c, &s);
                 __syncthreads();
-                if (!do_rot) continue;
-                if (threadIdx.x == 0) atomicAdd(rot + sweeps, 1);
+                if (do_rot && threadIdx.x == 0) atomicAdd(rot + sweeps, 1);
+                if (do_rot) {
 #pragma unroll
-                for (int u = 0; u < kCoopPer; u++) {
-                    const int r = threadIdx.x + u * kCoopThreads;
-                    if (r < t) {
-                        __stcg(bp + r, c * xb[u] - s * yb[u]);
-                        __stcg(bq + r, s * xb[u] + c * yb[u]);
-                        __stcg(wp + r, c * xw[u] - s * yw[u]);
-                        __stcg(wq + r, s * xw[u] + c * yw[u]);
+                    for (int u = 0; u < kCoopPer; u++) {
+                        const int r = threadIdx.x + u * kCoopThreads;
+                        if (r < t) {
+                            __stcg(bp + r, c * xb[u] - s * yb[u]);
+                            __stcg(bq + r, s * xb[u] + c * yb[u]);
+                            __stcg(wp + r, c * xw[u] - s * yw[u]);
+                            __stcg(wq + r, s * xw[u] + c * yw[u]);
+                        }
                     }
                 }
+                __syncthreads();  // every store of the CTA precedes the release below
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    st_release_u32(flag + p, R + 1);
+                    st_release_u32(flag + q, R + 1);
+                }
             }
-            if (!grid_sync(bar, nblk, timeout)) return;
         }
+        if (!grid_sync(bar, nblk, timeout)) return;  // once per sweep: the rotation count is final
         const int done = (__ldcg(rot + sweeps) == 0);
         sweeps++;
         if (done) { conv = true; break; }
@@ -381,7 +426,7 @@ cudaError_t small_svd(int t, const double *T, int64_t ldt, double *S, double *Uh
         return cudaGetLastError();
     }
     if (t > kCoopThreads * kCoopPer) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(w.bar, 0, (2 + (size_t)t) * sizeof(unsigned), s);  // barrier + column flags
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(w.rot, 0, sizeof(int) * w.max_sweeps, s);
     if (e != cudaSuccess) return e;

@@ -414,7 +414,7 @@ static int reserve_ws(svdsc_ctx *c, int t)
     alloc((void **)&c->svd.W, sizeof(double) * (size_t)t * t);
     alloc((void **)&c->svd.sig, sizeof(double) * t);
     alloc((void **)&c->svd.rot, sizeof(int) * c->svd.max_sweeps);
-    alloc((void **)&c->svd.bar, sizeof(unsigned) * 2);
+    alloc((void **)&c->svd.bar, sizeof(unsigned) * (2 + (size_t)t));  // grid barrier + Jacobi column flags
     if (!ok) {
         free_workspace(c);
         cudaGetLastError();
