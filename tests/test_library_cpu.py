@@ -81,3 +81,34 @@ def test_oracle_builds_independently():
         assert "oracle/" not in text and "svds_oracle" not in text and "orc_" not in text
     pkg_init = open(os.path.join(ROOT, "paper_2405_18966_gb300", "__init__.py")).read()
     assert "import oracle" not in pkg_init
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof / offsetof of a header struct, from a C program compiled against
+    the public header alone (plain C, no CUDA)."""
+    src = tmp_path / f"layout_{struct}.c"
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "svdsc.h"', "int main(void) {",
+             f'  printf("size %zu\\n", sizeof({struct}));']
+    lines += [f'  printf("{f} %zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / f"layout_{struct}"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    return {k: int(v) for k, v in (ln.split() for ln in out.splitlines())}
+
+
+@pytest.mark.parametrize("struct,cls", [("svdsc_matrix", "SvdscMatrix"), ("svdsc_options", "SvdscOptions"),
+                                        ("svdsc_info", "SvdscInfo")])
+def test_binding_struct_layouts_match_the_header(struct, cls, tmp_path):
+    """The ctypes mirrors in the Python binding have the header's size and
+    field offsets (the header is the contract; the binding only marshals)."""
+    import paper_2405_18966_gb300 as pkg
+    C = getattr(pkg, cls)
+    fields = [f for f, _ in C._fields_]
+    lay = _c_layout(struct, fields, tmp_path)
+    import ctypes
+    assert ctypes.sizeof(C) == lay["size"], (ctypes.sizeof(C), lay["size"])
+    for f in fields:
+        assert getattr(C, f).offset == lay[f], (f, getattr(C, f).offset, lay[f])
