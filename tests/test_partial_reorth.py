@@ -130,3 +130,49 @@ def test_gpu_partial_rejected_by_batch(pkg):
     k = np.array([5], dtype=np.int32)
     rc = p.lib().svdsc_batch_create(C.byref(h), 1, arr, p._ptr(k), p._ptr(k), C.byref(opt), None)
     assert rc == p.ERR_ARG
+
+
+# ------------------------------------------------------------------ combinations
+
+def _separated():
+    s = np.linspace(2.0, 1.0, 200)
+    s[-5:] = [0.3, 0.2, 0.1, 0.05, 0.01]
+    return synth.dense_prescribed(300, 200, s, 11)
+
+
+def test_oracle_partial_with_smallest(orc):
+    """Both options together: the five separated smallest values of the
+    closed form, basis orthogonal to the eps^(3/4) level."""
+    d = _separated()
+    r = orc.svds(d.a, 5, 25, 1e-10, 500, which="smallest", reorth="partial", return_basis=True,
+                 v0=synth.start_vector(200, 1))
+    assert r["info"]["converged"] == 1
+    np.testing.assert_allclose(r["S"], np.sort(d.s)[:5], rtol=0, atol=1e-13)
+    assert _orth_loss(r["Ub"]) < ORTH and _orth_loss(r["Vb"][:, :-1]) < ORTH
+    assert r["info"]["n_reorth"] < r["info"]["n_steps"] - 1
+
+
+@pytest.mark.gpu
+def test_gpu_partial_with_smallest(pkg, orc):
+    d = _separated()
+    v0 = synth.start_vector(200, 1)
+    r = pkg.svds(d.a, 5, 25, 1e-10, 500, v0=v0, which="smallest", reorth="partial")
+    ref = orc.svds(d.a, 5, 25, 1e-10, 500, v0=v0, which="smallest", reorth="partial")
+    assert r.info["converged"] == 1
+    np.testing.assert_allclose(r.S, ref["S"], rtol=1e-10)
+    np.testing.assert_allclose(r.S, np.sort(d.s)[:5], rtol=0, atol=1e-13)
+    assert _orth_loss(r.V) < ORTH
+
+
+@pytest.mark.gpu
+def test_gpu_partial_with_mixed_precision(pkg, orc):
+    """Mixed precision (FP32 products and first CGS pass) with the partial
+    scheme: singular values within the mixed form's 1e-6 of the FP64 oracle."""
+    a = synth.workload_sparse_small_fp32()
+    v0 = synth.start_vector(a.n, 4)
+    ref = orc.svds(a, 20, 20, 1e-10, 200, v0=v0)
+    a32 = synth.CSR(a.m, a.n, a.row_ptr, a.col_idx, a.values.astype(np.float32))
+    r = pkg.svds(a32, 20, 20, 1e-10, 200, precision="mixed", v0=v0, reorth="partial")
+    assert r.info["converged"] == 1
+    np.testing.assert_allclose(r.S, ref["S"], rtol=1e-6)
+    assert r.info["n_reorth"] < r.info["n_steps"] - 1
