@@ -114,12 +114,12 @@ typedef struct svdsc_options {
 
 /* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
 enum svdsc_phase {
-    SVDSC_PH_SPMV = 0,     /* products with A and A^T (Alg. 1 lines 2, 5, 7) */
+    SVDSC_PH_SPMV = 0,     /* products with A and A^T (Alg. 1) */
     SVDSC_PH_GEMV_T = 1,   /* CGS projections h = W^T w */
     SVDSC_PH_GEMV_N = 2,   /* CGS updates w -= W h */
     SVDSC_PH_VEC = 3,      /* ordered reductions, norms, scaling (finalize) */
-    SVDSC_PH_SVD = 4,      /* projected SVD (Alg. 2 line 4) */
-    SVDSC_PH_GEMM = 5,     /* restart / output basis update (Alg. 2 lines 8, 15) */
+    SVDSC_PH_SVD = 4,      /* projected SVD (Alg. 2) */
+    SVDSC_PH_GEMM = 5,     /* restart / output basis update (Alg. 2) */
     SVDSC_PH_OTHER = 6,    /* residual test, T rebuild, sign rule, copies */
     SVDSC_NUM_PHASES = 8
 };
@@ -165,7 +165,7 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
 /*
  * Alg. 2: k largest singular triplets (k smallest if the context was created
  * with which = SVDSC_SMALLEST).
- *   t = k + p (p < 0: t = max(15, 3k), Alg. 2 line 1); needs 1 <= k <= t,
+ *   t = k + p (p < 0: t = max(15, 3k), Alg. 2); needs 1 <= k <= t,
  *   t <= m and t + 1 <= n, k <= 256 and t <= 512 (t <= 448 with the
  *   tensor-core restart GEMM) (SVDSC_ERR_SIZE otherwise).
  *   tol: relative residual tolerance of Eq. (4), > 0 (the paper uses 1e-10).
@@ -199,8 +199,8 @@ const char *svdsc_strerror(int status);
  */
 
 /*
- * y = A x (trans = 0, Alg. 1 line 7, x: n, y: m) or y = A^T x (trans = 1,
- * Alg. 1 line 5, x: m, y: n), minus coef * z when z != NULL (the fused
+ * y = A x (trans = 0, Alg. 1, x: n, y: m) or y = A^T x (trans = 1,
+ * Alg. 1, x: m, y: n), minus coef * z when z != NULL (the fused
  * "- beta_i u_i" / "- alpha_i v_i" term).  FP64 vectors; in MIXED contexts the
  * sparse product itself runs in FP32 as in the solver.  Device pointers.
  */
@@ -219,7 +219,7 @@ int svdsc_cgs2(svdsc_ctx *ctx, int64_t len, int64_t ncols, const double *W, int6
                double *w, double *norm_out);
 
 /*
- * Projected SVD of Alg. 2 line 4 on the device: T is t x t (ldt >= t), any
+ * Projected SVD of Alg. 2 on the device: T is t x t (ldt >= t), any
  * square matrix (the solver passes the upper-triangular T(1:t,1:t)).  Outputs
  * S[t] descending, Uh (t x t, ld t) and Vh (t x t, ld t) with T = Uh diag(S)
  * Vh^T.  FP64 one-sided Jacobi.  Device pointers; t <= t_max.
@@ -232,7 +232,7 @@ int svdsc_small_svd(svdsc_ctx *ctx, int t, const double *T, int64_t ldt, double 
 int svdsc_reserve(svdsc_ctx *ctx, int t);
 
 /*
- * Restart / output basis update of Alg. 2 lines 8 and 15 on the tensor cores:
+ * Restart / output basis update of Alg. 2 on the tensor cores:
  * C = W Q with W rows x t (leading dimension ldw), Q t x k (ldq), C rows x k
  * (ldc), all column-major FP64 device arrays; C must not overlap W.
  *   mode 0 (FP64 form): both operands are cut into nine signed 6-bit digit

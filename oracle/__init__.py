@@ -129,7 +129,7 @@ def get_threads() -> int:
 
 
 def matvec(A, x):
-    """y = A x (Alg. 1 lines 2, 7)."""
+    """y = A x (Alg. 1)."""
     b = _Bound(A)
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty(b.m)
@@ -138,7 +138,7 @@ def matvec(A, x):
 
 
 def matvec_t(A, x):
-    """y = A^T x (Alg. 1 line 5)."""
+    """y = A^T x (Alg. 1)."""
     b = _Bound(A)
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty(b.n)

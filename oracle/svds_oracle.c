@@ -65,7 +65,7 @@ int orc_get_threads(void)
 
 /* ---------------------------------------------------------------- products */
 
-/* y = A x  (Alg. 1 lines 2 and 7). */
+/* y = A x  (Alg. 1). */
 void orc_matvec(const orc_mat *A, const double *x, double *y)
 {
     if (A->kind == 0) {
@@ -92,7 +92,7 @@ void orc_matvec(const orc_mat *A, const double *x, double *y)
     }
 }
 
-/* y = A^T x  (Alg. 1 line 5). */
+/* y = A^T x  (Alg. 1). */
 void orc_matvec_t(const orc_mat *A, const double *x, double *y)
 {
     if (A->kind == 0) {
@@ -165,7 +165,7 @@ double orc_norm2(int64_t len, const double *x)
 }
 
 /* C (rows x kk, ldc) = W (rows x tt, ldw) * Q (tt x kk, ldq): the restart
- * update of Alg. 2 line 8 and the final product of line 15. */
+ * update of Alg. 2 and its final product. */
 void orc_gemm_nn(int64_t rows, int64_t tt, int64_t kk, const double *W, int64_t ldw,
                  const double *Q, int64_t ldq, double *C, int64_t ldc)
 {
@@ -540,7 +540,7 @@ void orc_sign_normalize(int64_t m, int64_t n, int64_t k, double *U, int64_t ldu,
  * of the spectrum, Sec. 2; the same restart keeps the k smallest Ritz
  * triplets instead of the k largest; needs m >= n so that the n singular
  * values of A are those of A^T A).
- *   t = k + p (p < 0: t = max(15, 3k) as in Alg. 2 line 1); requires
+ *   t = k + p (p < 0: t = max(15, 3k) as in Alg. 2); requires
  *   1 <= k <= t, t + 1 <= min(m, n) ... t <= m and t + 1 <= n.
  *   maxit: number of small-SVD-and-residual-test rounds (>= 1).
  *   reorth: 0 re-orthogonalizes every Lanczos vector (CGS2, Sec. 2.1); 1 only
@@ -591,7 +591,7 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
         return -4;
     }
 
-    /* Alg. 1 line 1: v_1 = randn(n), normalised (or the caller's v0) */
+    /* Alg. 1, start: v_1 = randn(n), normalised (or the caller's v0) */
     if (v0) memcpy(L.wn, v0, sizeof(double) * (size_t)n);
     else orc_rng_vector(seed, L.draws++, n, L.wn);
     if (v0) L.draws++;  /* draw 0 is reserved for the start vector either way */
@@ -603,20 +603,20 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
         }
         for (int64_t r = 0; r < n; r++) L.V[r] = L.wn[r] / nv;
     }
-    /* lines 2-3: u_1 = A v_1, alpha_1 = ||u_1||, u_1 /= alpha_1 */
+    /* u_1 = A v_1, alpha_1 = ||u_1||, u_1 /= alpha_1 */
     orc_matvec(A, L.V, L.wm);
     info->n_matvec++;
     T_(&L, 0, 0) = orc_finish_vector(&L, L.wm, m, L.U, 0);
     info->n_steps++;
     L.nu[0] = 1.0;   /* v_1^T v_1 */
     L.mu[0] = 1.0;   /* u_1^T u_1 */
-    /* Alg. 2 line 2: LBP(A, t+1) */
+    /* Alg. 2: LBP(A, t+1) */
     orc_lbp_from(&L, 1);
 
     int64_t it;
     for (it = 1; it <= maxit; it++) {
         if (info->stopped_early) break;
-        /* line 4: SVD of T(1:t,1:t) */
+        /* Alg. 2: SVD of T(1:t,1:t) */
         for (int64_t c = 0; c < t; c++)
             for (int64_t r = 0; r < t; r++) Tt[r + c * t] = T_(&L, r, c);
         int sw = orc_jacobi_svd(t, t, Tt, t, Sh, Uh, t, Vh, t, 200);
@@ -635,7 +635,7 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
                 }
             }
         }
-        /* line 5 / Eq. (4): res_j = |beta_t Uh(t,j)| / sigma_j */
+        /* Eq. (4): res_j = |beta_t Uh(t,j)| / sigma_j */
         double beta_t = T_(&L, t - 1, t);
         info->beta_t = beta_t;
         int64_t nconv = 0;
@@ -649,7 +649,7 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
         info->converged = (nconv == k);
         if (info->converged || it == maxit) break;
 
-        /* lines 8-12: augmented restart */
+        /* augmented restart (Eq. 5-7) */
         orc_gemm_nn(m, t, k, L.U, m, Uh, t, Uk, m);          /* U~_k = U(:,1:t) Uh(:,1:k) */
         orc_gemm_nn(n, t, k, L.V, n, Vh, t, Vk, n);          /* V~_k = V(:,1:t) Vh(:,1:k) */
         if (L.reorth) {
@@ -685,11 +685,11 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
         L.mu[k] = 1.0;
         info->n_steps++;
         info->restarts++;
-        /* line 12: continue Alg. 1 from i = k+1 */
+        /* continue Alg. 1 from i = k+1 */
         orc_lbp_from(&L, k + 1);
     }
     if (!info->stopped_early) {
-        /* lines 14-15: S, U~ = U(:,1:t) Uh(:,1:k), V~ = V(:,1:t) Vh(:,1:k) */
+        /* outputs: S, U~ = U(:,1:t) Uh(:,1:k), V~ = V(:,1:t) Vh(:,1:k) */
         for (int64_t j = 0; j < k; j++) S[j] = Sh[j];
         orc_gemm_nn(m, t, k, L.U, m, Uh, t, Uout, ldu);
         orc_gemm_nn(n, t, k, L.V, n, Vh, t, Vout, ldv);

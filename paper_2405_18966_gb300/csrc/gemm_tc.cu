@@ -1,5 +1,5 @@
-// Restart / output basis update of Alg. 2 (lines 8 and 15 of the svds-C
-// paper): C (rows x k) = W (rows x t) Q (t x k), W tall and skinny, on the
+// Restart / output basis update of Alg. 2 (the restart and the final
+// output of the svds-C paper): C (rows x k) = W (rows x t) Q (t x k), W tall and skinny, on the
 // 5th-generation tensor cores (tcgen05.mma, accumulators in TMEM).
 //
 // Operands are cut into BF16 "slices" and the slice pairs that matter are

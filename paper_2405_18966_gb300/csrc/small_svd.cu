@@ -1,4 +1,4 @@
-// Projected SVD of Alg. 2 line 4 (svds-C paper): [Uh, Sh, Vh] = svd(T(1:t,1:t))
+// Projected SVD of Alg. 2 (svds-C paper): [Uh, Sh, Vh] = svd(T(1:t,1:t))
 // in FP64 on the device, by one-sided (Hestenes) Jacobi: columns of B = T V
 // are rotated in pairs until mutually orthogonal; sigma_j = ||B(:,j)||,
 // uh_j = B(:,j)/sigma_j, vh_j = the accumulated rotation.  Pairs are visited

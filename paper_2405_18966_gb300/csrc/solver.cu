@@ -131,7 +131,7 @@ static inline int *poison_ptr(svdsc_ctx *c) { return &c->st->poison; }
 
 // Eq. (4) residuals res_j = |beta_t Uh(t,j)| / max(sigma_j, eps sigma_1), the
 // restart coefficients rho_j = beta_t Uh(t,j) of Eq. (6), the convergence test
-// of Alg. 2 line 5 and the ||A|| estimate.
+// of Alg. 2 and the ||A|| estimate.
 __global__ void residual_kernel(int t, int k, double tol, const double *__restrict__ T,
                                 const double *__restrict__ Sh, const double *__restrict__ Uh,
                                 double *__restrict__ res, double *__restrict__ rho, DevStatus *st,
@@ -183,7 +183,7 @@ __global__ void reverse_triplets_kernel(int t, double *__restrict__ Sh, double *
         }
 }
 
-// T <- 0; T(j,j) = sigma_j, T(j,k+1) = rho_j for j <= k  (Alg. 2 line 9)
+// T <- 0; T(j,j) = sigma_j, T(j,k+1) = rho_j for j <= k  (the augmented restart of Alg. 2, Eq. 6)
 __global__ void restart_T_kernel(int t, int k, double *__restrict__ T, const double *__restrict__ Sh,
                                  const double *__restrict__ rho)
 {
@@ -199,8 +199,8 @@ __global__ void restart_T_kernel(int t, int k, double *__restrict__ T, const dou
         }
 }
 
-// In-place restart update W(:, 0:k) <- W(:, 0:t) Q(:, 0:k) of Alg. 2 line 8 /
-// line 15 (FP64 FMA).  A CTA owns a block of 32 rows and all k outputs of
+// In-place restart update W(:, 0:k) <- W(:, 0:t) Q(:, 0:k) of Alg. 2 (restart
+// and final output, FP64 FMA).  A CTA owns a block of 32 rows and all k outputs of
 // them, so it reads its rows completely before overwriting them.  Q is held in
 // shared memory in chunks of KC rows.
 constexpr int kGemmGroups = 8;   // warps per CTA; each covers 32 rows x (k / 8) columns
@@ -533,7 +533,7 @@ static void reorth_vector(svdsc_ctx *c, int side, int ncols, double *w)
     cgs2(c, W, W32, ld, ncols, w, ch, &c->pr->gate, false);
 }
 
-// v_{i+1} = A^T u_i - alpha_i v_i, re-orthogonalized against v_1..v_i, beta_i = ||.||  (Alg. 1 lines 5-6)
+// v_{i+1} = A^T u_i - alpha_i v_i, re-orthogonalized against v_1..v_i, beta_i = ||.||  (Alg. 1)
 static int issue_v(svdsc_ctx *c, int i)
 {
     double *out = colV(c, i);
@@ -545,7 +545,7 @@ static int issue_v(svdsc_ctx *c, int i)
     return SVDSC_OK;
 }
 
-// u_{i+1} = A v_{i+1} - beta_i u_i, re-orthogonalized against u_1..u_i, alpha_{i+1}  (Alg. 1 lines 7-8)
+// u_{i+1} = A v_{i+1} - beta_i u_i, re-orthogonalized against u_1..u_i, alpha_{i+1}  (Alg. 1)
 static int issue_u(svdsc_ctx *c, int i)
 {
     double *out = colU(c, i);
@@ -798,7 +798,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     }
     CU(cudaMemsetAsync(c->T, 0, sizeof(double) * (size_t)(t + 1) * (t + 1), s));
 
-    // Alg. 1 line 1: v_1 (the caller's v0 or draw 0), normalised
+    // Alg. 1, start: v_1 (the caller's v0 or draw 0), normalised
     if (v0) CU(cudaMemcpyAsync(colV(c, 0), v0, sizeof(double) * c->n,
                                v0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     else { rng_normal_vec(c->seed, 0, c->n, colV(c, 0), s); ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0); }
@@ -822,13 +822,13 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     }
     c->steps.clear();   // step ids below index Lanczos vectors only
     c->n_steps = 0;
-    // lines 2-3: u_1 = A v_1, alpha_1
+    // u_1 = A v_1, alpha_1
     rc = apply_A(c, 0, colV(c, 0), colV32(c, 0), nullptr, nullptr, 0.0, colU(c, 0), poison_ptr(c));
     if (rc) return rc;
     norm_partial(colU(c, 0), c->cm, c->Pn, poison_ptr(c), s);
     ph_end(c, SVDSC_PH_VEC, -1, 1, 8.0 * c->m, 2.0 * c->m);
     do_finalize(c, 0, 0, Tent(c, 0, 0), 0);
-    // Alg. 2 line 2: LBP(A, t+1)
+    // Alg. 2: LBP(A, t+1)
     rc = issue_segment(c, 1, false);
     if (rc) return rc;
     rc = settle(c);
@@ -836,7 +836,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
 
     int restarts = 0;
     for (int it = 1; it <= maxit; it++) {
-        // line 4: SVD of T(1:t,1:t)
+        // Alg. 2: SVD of T(1:t,1:t)
         {
             const int e0 = ph_begin(c);
             CU(small_svd(t, c->T, t + 1, c->Sh, c->Uh, c->Vh, c->svd, c->st, s, nullptr));
@@ -848,7 +848,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
             }
             ph_end(c, SVDSC_PH_SVD, e0, nl, 0.0, 0.0);
         }
-        // line 5: residual test (Eq. 4)
+        // residual test (Eq. 4)
         {
             const int e0 = ph_begin(c);
             residual_kernel<<<1, 256, 0, s>>>(t, k, tol, c->T, c->Sh, c->Uh, c->res, c->rho, c->st, c->parity,
@@ -860,7 +860,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         if (rc) return rc;
         if (c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
         if (c->st_host->converged || it == maxit) break;
-        // lines 8-12: augmented restart
+        // augmented restart (Eq. 5-7)
         if (c->restart_gemm == 0) {
             // U~_k = U(:,1:t) Uh(:,1:k), V~_k = V(:,1:t) Vh(:,1:k) into the other bases
             rc = gemm_tc(c, c->U, c->U32, c->ldu, c->m, t, c->Uh, k, c->Ua, c->U32a);
@@ -908,7 +908,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         cgs2(c, c->U, c->U32, c->ldu, k, colU(c, k), c->cm, poison_ptr(c));
         do_finalize(c, 0, k, Tent(c, k, k), 0);
         restarts++;
-        // line 12: continue Alg. 1 from i = k+1
+        // continue Alg. 1 from i = k+1
         rc = issue_segment(c, k + 1, false);
         if (rc) return rc;
         rc = settle(c);
@@ -916,7 +916,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     }
     const DevStatus fin = *c->st_host;
 
-    // lines 14-15: outputs (into the spare bases or in place, then copied out)
+    // outputs of Alg. 2 (into the spare bases or in place, then copied out)
     double *Uo = c->U, *Vo = c->V;
     if (c->restart_gemm == 0) {
         rc = gemm_tc(c, c->U, c->U32, c->ldu, c->m, t, c->Uh, k, c->Ua, nullptr);

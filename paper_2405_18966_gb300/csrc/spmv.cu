@@ -1,4 +1,4 @@
-// Products with A and A^T (Alg. 1 lines 2, 5 and 7 of the svds-C paper):
+// Products with A and A^T (Alg. 1 of the svds-C paper):
 // a row-length-binned CSR SpMV (one launch covers every bin), dense
 // column-major GEMV / GEMV-T, and the create-time preparation of CSR(A) and
 // CSR(A^T) (0-based compaction, validation, deterministic transpose, bins).

@@ -299,7 +299,7 @@ def test_max_size_and_bad_args(orc):
             orc.svds(A, bad["k"], bad["p"], 1e-10, 10)
     with pytest.raises(ValueError):
         orc.svds(A, 2, 2, 0.0, 10)
-    # default subspace dimension of Alg. 2 line 1
+    # default subspace dimension of Alg. 2
     assert orc.subspace_dim(3, -1) == 15 and orc.subspace_dim(10, -1) == 30
 
 
