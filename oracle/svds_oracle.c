@@ -23,7 +23,11 @@
  * round never restarts; a Lanczos vector whose norm falls to 1e-13 * (largest
  * alpha/beta/sigma seen) is a breakdown, its T entry is set to zero and a fresh
  * random vector, orthogonalized against the basis, takes its place; the
- * residual denominator is max(sigma_j, eps*sigma_1).
+ * residual denominator is max(sigma_j, eps*sigma_1).  Two options beyond the
+ * paper's default: the k smallest triplets (the same restart keeping the k
+ * smallest Ritz triplets, S ascending, m >= n) and partial
+ * re-orthogonalization (orthogonality estimates from the Lanczos relations
+ * decide which vectors get CGS2, threshold eps^(3/4)).
  */
 #include <float.h>
 #include <math.h>
