@@ -585,7 +585,10 @@ def main():
     dom = max(cand, key=lambda ph: tot["ms"][ph])
     n_l = max(1, tot["launches"][dom])
     avg_ms = tot["ms"][dom] / n_l
-    if dom in ("gemv_t", "gemv_n", "gemm") and prec == "fp64":
+    # FP64 GEMVs (and the dense product, one FMA per 8-byte element) are capped by
+    # the FP64 FMA rate (4.8 TB/s-equivalent) before HBM: report them as ALU-bound
+    alu_bound = dom in ("gemv_t", "gemv_n", "gemm") or (dom == "spmv" and not hasattr(A, "row_ptr"))
+    if alu_bound and prec == "fp64":
         ach = tot["flops"][dom] / n_l / (avg_ms * 1e-3) / 1e12
         tr = TRAFFIC_RATIO.get(dom)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
