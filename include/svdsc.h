@@ -219,6 +219,20 @@ int svdsc_cgs2(svdsc_ctx *ctx, int64_t len, int64_t ncols, const double *W, int6
                double *w, double *norm_out);
 
 /*
+ * Self-test of the bounded device-side waits (the paper has no counterpart).
+ * Every spin-wait in the library's kernels gives up after an iteration limit,
+ * records the timeout in the context's status block and lets its kernel
+ * return, so a wait that can never be satisfied ends in SVDSC_ERR_TIMEOUT
+ * instead of a hung GPU.  This call makes one such wait run out on purpose:
+ * kind 0, the grid barrier of the multi-CTA Jacobi SVD (a cooperative launch
+ * of 4 CTAs that each wait for a fifth arrival); kind 1, the mbarrier wait of
+ * the tensor-core GEMM (nothing ever arrives).  It takes a few seconds (the
+ * real limits), returns SVDSC_ERR_TIMEOUT when the wait ran out as designed
+ * (SVDSC_OK would mean it did not), and leaves the context usable.
+ */
+int svdsc_selftest_wait(svdsc_ctx *ctx, int kind);
+
+/*
  * Projected SVD of Alg. 2 on the device: T is t x t (ldt >= t), any
  * square matrix (the solver passes the upper-triangular T(1:t,1:t)).  Outputs
  * S[t] descending, Uh (t x t, ld t) and Vh (t x t, ld t) with T = Uh diag(S)

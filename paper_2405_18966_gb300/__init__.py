@@ -33,7 +33,8 @@ F64, F32 = 0, 1
 EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "svdsc_matvec",
            "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc",
            "svdsc_gemm", "svdsc_batch_create", "svdsc_batch_solve", "svdsc_batch_tuning",
-           "svdsc_batch_destroy", "svdsc_solve_batched", "svdsc_batch_layout", "svdsc_batch_profile")
+           "svdsc_batch_destroy", "svdsc_solve_batched", "svdsc_batch_layout", "svdsc_batch_profile",
+           "svdsc_selftest_wait")
 
 
 class SvdscMatrix(C.Structure):
@@ -103,6 +104,7 @@ def lib():
         L.svdsc_batch_destroy.argtypes = [vp]
         L.svdsc_batch_layout.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.svdsc_batch_profile.argtypes = [vp, vp, vp, vp, vp]
+        L.svdsc_selftest_wait.argtypes = [vp, i32]
         L.svdsc_solve_batched.argtypes = [i32, C.POINTER(SvdscMatrix), vp, vp, dbl, i32, vp, vp, vp, vp,
                                           i32, C.POINTER(SvdscOptions), C.POINTER(SvdscInfo)]
         for name in EXPORTS:
@@ -280,6 +282,11 @@ class Solver:
         _check(lib().svdsc_gemm(self.handle, mode, rows, t, k, _ptr(Wc), rows, _ptr(Qc), t, _ptr(Ct), rows),
                "svdsc_gemm")
         return Ct.t()
+
+    def selftest_wait(self, kind: int) -> int:
+        """Makes one bounded device wait run out on purpose (0: grid barrier,
+        1: mbarrier); returns the status code (TIMEOUT is the designed outcome)."""
+        return lib().svdsc_selftest_wait(self.handle, int(kind))
 
     def small_svd(self, T):
         """T: t x t torch CUDA float64 tensor; returns (S, Uh, Vh) with T = Uh diag(S) Vh^T."""

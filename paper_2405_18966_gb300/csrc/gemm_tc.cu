@@ -48,16 +48,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)  // suspend at most ~1 us per try
         : "memory");
     return ok != 0;
 }
 
-// Bounded wait: gives up after ~2^22 polls (each try_wait also suspends for a
-// hardware-chosen interval) and reports the timeout instead of hanging.
+// Bounded wait: gives up after 2^22 polls (each try_wait suspends for at most
+// ~1 us, so ~4 s in all) and reports the timeout instead of hanging.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
     for (uint32_t i = 0; i < (1u << 22); i++)
@@ -628,6 +628,25 @@ static cudaError_t launch_tc(const WT *W, int64_t ldw, int64_t rows, int t, cons
 }
 
 // mode 0: FP64 (Ozaki digits), mode 1: three BF16 pieces with FP32 accumulation.
+// Self-test of the bounded mbarrier wait: nothing arrives on the barrier, so
+// mbar_wait_bounded must give up; the kernel records it in *err and returns.
+__global__ void mbar_probe_kernel(int *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0)) atomicExch(err, 1);
+}
+
+cudaError_t probe_mbarrier(int *err, cudaStream_t s)
+{
+    mbar_probe_kernel<<<1, 32, 0, s>>>(err);
+    return cudaGetLastError();
+}
+
 cudaError_t tc_gemm(int mode, const double *W, const float *W32, int64_t ldw, int64_t rows, int t,
                     const double *Q, int64_t ldq, int k, double *C, int64_t ldc, float *C32, void *ws,
                     int *err, cudaStream_t s, int *launches)

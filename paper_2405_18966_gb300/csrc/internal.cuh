@@ -154,6 +154,9 @@ struct SvdWork {
 cudaError_t small_svd(int t, const double *T, int64_t ldt, double *S, double *Uh, double *Vh,
                       SvdWork &w, DevStatus *st, cudaStream_t s, int *launches);
 int small_svd_coop_capacity();
+// self-tests of the bounded waits (each wait is made to run out on purpose)
+cudaError_t probe_grid_barrier(unsigned *bar, DevStatus *st, cudaStream_t s);
+cudaError_t probe_mbarrier(int *err, cudaStream_t s);
 
 // ---- tensor-core restart GEMM (gemm_tc.cu)
 size_t tc_gemm_ws_bytes(int t, int k);

@@ -398,6 +398,23 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
     }
 }
 
+// Self-test of the bounded grid barrier: every CTA waits for one more arrival
+// than the grid has, so the wait must run out; grid_sync records the timeout
+// in the status block and each CTA returns.
+__global__ void barrier_probe_kernel(unsigned *bar, DevStatus *st)
+{
+    grid_sync(bar, gridDim.x + 1, &st->timeout);
+}
+
+cudaError_t probe_grid_barrier(unsigned *bar, DevStatus *st, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&bar, &st};
+    return cudaLaunchCooperativeKernel((const void *)barrier_probe_kernel, dim3(4), dim3(kCoopThreads), args,
+                                       0, s);
+}
+
 int small_svd_coop_capacity()
 {
     int dev = 0, nsm = 0, per = 0;

@@ -282,7 +282,7 @@ static int gemm_tc(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, 
     cudaError_t e = tc_gemm(mode, W, W32, ld, rows, t, Q, t, k, C, ld, C32, c->gemm_ws, &c->st->timeout,
                             c->stream, &nl);
     const double wb = (W32 ? 4.0 : 8.0) * rows * t;
-    const double prods = mode == 0 ? 45.0 : 6.0;
+    const double prods = mode == 0 ? 36.0 : 6.0;  // BF16 products per multiply-add
     ph_end(c, SVDSC_PH_GEMM, e0, nl, wb + 8.0 * rows * k + (C32 ? 4.0 * rows * k : 0.0),
            2.0 * rows * (double)t * k * prods);
     return e == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
@@ -1029,6 +1029,26 @@ int svdsc_gemm(svdsc_ctx *c, int mode, int64_t rows, int t, int k, const double 
     int rc = read_status(c);
     if (rc) return rc;
     return c->st_host->timeout ? SVDSC_ERR_TIMEOUT : SVDSC_OK;
+}
+
+int svdsc_selftest_wait(svdsc_ctx *c, int kind)
+{
+    if (!c || (kind != 0 && kind != 1)) return SVDSC_ERR_ARG;
+    int rc = reserve_ws(c, 2);  // the status block and the barrier words
+    if (rc) return rc;
+    DevStatus init;
+    memset(&init, 0, sizeof(init));
+    init.bd_step = INT_MAX;
+    CU(cudaMemcpyAsync(c->st, &init, sizeof(DevStatus), cudaMemcpyHostToDevice, c->stream));
+    if (kind == 0) CU(probe_grid_barrier(c->svd.bar, c->st, c->stream));
+    else CU(probe_mbarrier(&c->st->timeout, c->stream));
+    rc = read_status(c);
+    if (rc) return rc;
+    const int ran_out = c->st_host->timeout;
+    init.timeout = 0;  // leave the context as a solve expects it
+    CU(cudaMemcpyAsync(c->st, &init, sizeof(DevStatus), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return ran_out ? SVDSC_ERR_TIMEOUT : SVDSC_OK;
 }
 
 int svdsc_small_svd(svdsc_ctx *c, int t, const double *T, int64_t ldt, double *S, double *Uh, double *Vh)
