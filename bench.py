@@ -630,7 +630,7 @@ def main():
         hout = (pin(np.zeros(k)).numpy(), pin(np.zeros((k, A.m))).numpy().T,
                 pin(np.zeros((k, A.n))).numpy().T, pin(np.zeros(k)).numpy())
         d2h = sum(x.nbytes for x in hout)
-        times, creates = [], []
+        times, creates, solves = [], [], []
         for it in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -638,15 +638,18 @@ def main():
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
                 r2 = s2.solve(k, p, tol, maxit, v0=hv0, outputs=hout)
+                t2 = time.perf_counter()
             torch.cuda.synchronize()
             if it > 0:
                 times.append(time.perf_counter() - t0)
                 creates.append(t1 - t0)
+                solves.append(t2 - t1)
         ev = allreduce_max(statistics.median(times), ws)
         e2e = {"value": ev, "unit": "s", "h2d_bytes_per_step": int(h2d + hv0.nbytes),
                "d2h_bytes_per_step": int(d2h), "includes": "svdsc_create (upload, CSR(A^T), bins) + solve + "
                "copy of S, U, V, res to pinned host memory + destroy",
-               "create_s": statistics.median(creates)}
+               "create_s": statistics.median(creates),
+               "solve_with_host_outputs_s": statistics.median(solves)}
         launches_e2e = r2.info["n_launches"]
 
     cpu = None
