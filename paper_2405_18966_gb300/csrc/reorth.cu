@@ -224,6 +224,22 @@ update_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__r
                 }
             } else {
                 float f0 = 0.f, f1 = 0.f, g0 = 0.f, g1 = 0.f;
+                // four 8-byte loads in flight per thread (the FP32 pass is HBM-bound);
+                // same accumulation order as the two-column loop below
+                for (; c + 3 < ncols; c += 4) {
+                    const float2 v0 = __ldcs((const float2 *)(p + (int64_t)c * ld));
+                    const float2 v1 = __ldcs((const float2 *)(p + (int64_t)(c + 1) * ld));
+                    const float2 v2 = __ldcs((const float2 *)(p + (int64_t)(c + 2) * ld));
+                    const float2 v3 = __ldcs((const float2 *)(p + (int64_t)(c + 3) * ld));
+                    f0 = fmaf(v0.x, hs32[c], f0);
+                    f1 = fmaf(v0.y, hs32[c], f1);
+                    g0 = fmaf(v1.x, hs32[c + 1], g0);
+                    g1 = fmaf(v1.y, hs32[c + 1], g1);
+                    f0 = fmaf(v2.x, hs32[c + 2], f0);
+                    f1 = fmaf(v2.y, hs32[c + 2], f1);
+                    g0 = fmaf(v3.x, hs32[c + 3], g0);
+                    g1 = fmaf(v3.y, hs32[c + 3], g1);
+                }
                 for (; c + 1 < ncols; c += 2) {
                     const float2 v0 = __ldcs((const float2 *)(p + (int64_t)c * ld));
                     const float2 v1 = __ldcs((const float2 *)(p + (int64_t)(c + 1) * ld));
