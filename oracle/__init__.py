@@ -84,7 +84,7 @@ def lib():
             L.orc_jacobi_svd.restype = C.c_int
             L.orc_sign_normalize.argtypes = [i64, i64, i64, vp, i64, vp, i64]
             L.orc_svds.argtypes = [C.POINTER(_Mat), i64, i64, dbl, i64, i64, i64, C.c_uint64, vp, i64,
-                                   vp, vp, i64, vp, i64, vp, C.POINTER(Info), vp, vp, vp]
+                                   vp, vp, i64, vp, i64, vp, C.POINTER(Info), vp, vp, vp, vp, vp]
             L.orc_svds.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
@@ -233,9 +233,10 @@ def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, seed: int
     the orthogonality estimates ask for it.
 
     Returns a dict with S (k), U (m x k), V (n x k), res (k), info (dict) and,
-    if ``return_basis``, the final Lanczos basis Ub (m x t), Vb (n x (t+1))
-    and projected matrix T ((t+1) x (t+1)).  Raises ValueError on bad
-    arguments."""
+    if ``return_basis``, the final Lanczos basis Ub (m x t), Vb (n x (t+1)),
+    projected matrix T ((t+1) x (t+1)) and, for reorth="partial", the last
+    orthogonality estimates mu (u_t against u_1..u_{t-1}) and nu (v_{t+1}
+    against v_1..v_t).  Raises ValueError on bad arguments."""
     b = _Bound(A)
     m, n = b.m, b.n
     t = subspace_dim(k, p)
@@ -245,16 +246,18 @@ def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, seed: int
     res = np.zeros(k)
     info = Info()
     v0a = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64)
-    Ub = Vb = Tb = None
+    Ub = Vb = Tb = mu = nu = None
     if return_basis:
         Ub = np.zeros((m, t), order="F")
         Vb = np.zeros((n, t + 1), order="F")
         Tb = np.zeros((t + 1, t + 1), order="F")
+        mu = np.zeros(t + 2)
+        nu = np.zeros(t + 2)
     wh = {"largest": 0, "smallest": 1}[which]
     ro = {"full": 0, "partial": 1}[reorth]
     rc = lib().orc_svds(C.byref(b.mat), k, p, tol, maxit, wh, ro, C.c_uint64(seed), _ptr(v0a),
                         step_budget, _ptr(S), _ptr(U), m, _ptr(V), n, _ptr(res),
-                        C.byref(info), _ptr(Ub), _ptr(Vb), _ptr(Tb))
+                        C.byref(info), _ptr(Ub), _ptr(Vb), _ptr(Tb), _ptr(mu), _ptr(nu))
     if rc == -1:
         raise ValueError("bad arguments (need 1 <= k <= t, t <= m, t + 1 <= n, tol > 0, maxit >= 1; "
                          "m >= n for the smallest triplets)")
@@ -262,5 +265,5 @@ def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, seed: int
         raise MemoryError("oracle ran out of memory")
     out = {"S": S, "U": U, "V": V, "res": res, "info": info.as_dict(), "t": t}
     if return_basis:
-        out.update(Ub=Ub, Vb=Vb, T=Tb)
+        out.update(Ub=Ub, Vb=Vb, T=Tb, mu=mu, nu=nu)
     return out

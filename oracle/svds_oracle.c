@@ -552,14 +552,17 @@ void orc_sign_normalize(int64_t m, int64_t n, int64_t k, double *U, int64_t ldu,
  *   v0: start vector (length n) or NULL for the seeded random draw 0.
  *   Outputs: S (k), U (m x k, ldu), V (n x k, ldv), res (k).
  *   Optional (may be NULL): Ubasis (m x t), Vbasis (n x (t+1)),
- *   Tout ((t+1) x (t+1)) hold the final Lanczos basis and projected matrix.
+ *   Tout ((t+1) x (t+1)) hold the final Lanczos basis and projected matrix;
+ *   mu_out, nu_out (t+2 each) the last partial re-orthogonalization estimates
+ *   (newest u against the earlier u's, newest v against the earlier v's).
  * Returns 0 on success (converged or not: see info), -1 on bad arguments,
  * -4 if memory ran out.
  */
 int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, int64_t which,
              int64_t reorth, uint64_t seed, const double *v0, int64_t step_budget,
              double *S, double *Uout, int64_t ldu, double *Vout, int64_t ldv,
-             double *res, orc_info *info, double *Ubasis, double *Vbasis, double *Tout)
+             double *res, orc_info *info, double *Ubasis, double *Vbasis, double *Tout,
+             double *mu_out, double *nu_out)
 {
     memset(info, 0, sizeof(*info));
     const int64_t m = A->m, n = A->n;
@@ -703,6 +706,8 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
     if (Ubasis) memcpy(Ubasis, L.U, sizeof(double) * (size_t)(m * t));
     if (Vbasis) memcpy(Vbasis, L.V, sizeof(double) * (size_t)(n * (t + 1)));
     if (Tout) memcpy(Tout, L.T, sizeof(double) * (size_t)((t + 1) * (t + 1)));
+    if (mu_out) memcpy(mu_out, L.mu, sizeof(double) * (size_t)(t + 2));
+    if (nu_out) memcpy(nu_out, L.nu, sizeof(double) * (size_t)(t + 2));
 
     free(L.U); free(L.V); free(L.T); free(L.h); free(L.wm); free(L.wn); free(L.mu); free(L.nu);
     free(Uh); free(Vh); free(Sh); free(Tt); free(Uk); free(Vk); free(rho);

@@ -176,3 +176,28 @@ def test_gpu_partial_with_mixed_precision(pkg, orc):
     assert r.info["converged"] == 1
     np.testing.assert_allclose(r.S, ref["S"], rtol=1e-6)
     assert r.info["n_reorth"] < r.info["n_steps"] - 1
+
+
+@pytest.mark.parametrize("case", ["sparse", "decay"])
+def test_oracle_estimates_bound_the_true_inner_products(orc, case):
+    """The recurrences of the partial scheme estimate |v_{t+1}^T v_l| and
+    |u_t^T u_l|; against the final Lanczos vectors the estimates must bound
+    the true inner products (a dropped term or a wrong sign in either
+    recurrence makes them miss)."""
+    if case == "sparse":
+        A, k, p = synth.workload_sparse_small(), 10, 30
+        v0 = synth.start_vector(1000, 1)
+    else:
+        d = synth.workload_dense_decay(3, 0.03)
+        A, k, p, v0 = d.a, 10, 30, synth.start_vector(300, 1)
+    for maxit in (1, 2):            # end of the first LBP; after one restart
+        r = orc.svds(A, k, p, 1e-14, maxit, v0=v0, reorth="partial", return_basis=True)
+        t = r["t"]
+        U, V = r["Ub"], r["Vb"]
+        true_nu = np.abs(V[:, :t].T @ V[:, t])           # v_{t+1} against v_1..v_t
+        true_mu = np.abs(U[:, :t - 1].T @ U[:, t - 1])   # u_t against u_1..u_{t-1}
+        nu, mu = np.abs(r["nu"][:t]), np.abs(r["mu"][:t - 1])
+        assert np.all(true_nu <= 10 * nu + 1e-15), np.max(true_nu / (nu + 1e-300))
+        assert np.all(true_mu <= 10 * mu + 1e-15), np.max(true_mu / (mu + 1e-300))
+        # and they are estimates, not blanket bounds: within a few orders of the truth
+        assert np.max(nu) < 1e6 * max(np.max(true_nu), 1e-16)
