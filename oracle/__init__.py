@@ -87,6 +87,9 @@ def lib():
                                    vp, vp, i64, vp, i64, vp, C.POINTER(Info), vp, vp, vp, vp, vp]
             L.orc_svds.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
+            for f in ("orc_pr_nu_step", "orc_pr_mu_step"):
+                getattr(L, f).argtypes = [i64, vp, i64, vp, vp, dbl, dbl]
+                getattr(L, f).restype = dbl
             L.orc_get_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -218,6 +221,20 @@ def sign_normalize(U, V):
     lib().orc_sign_normalize(U.shape[0], V.shape[0], U.shape[1], _ptr(U), U.shape[0],
                              _ptr(V), V.shape[0])
     return U, V
+
+
+def pr_nu_step(i: int, T, mu, nu, beta: float, anorm: float) -> float:
+    """One step of the partial re-orthogonalization recurrence for v_{i+1}
+    (updates nu in place; T column-major (t+1) x (t+1)); returns the largest
+    new estimate."""
+    T = np.asfortranarray(T, dtype=np.float64)
+    return lib().orc_pr_nu_step(i, _ptr(T), T.shape[0], _ptr(mu), _ptr(nu), beta, anorm)
+
+
+def pr_mu_step(i: int, T, mu, nu, alpha: float, anorm: float) -> float:
+    """One step of the recurrence for u_{i+1} (updates mu in place)."""
+    T = np.asfortranarray(T, dtype=np.float64)
+    return lib().orc_pr_mu_step(i, _ptr(T), T.shape[0], _ptr(mu), _ptr(nu), alpha, anorm)
 
 
 def subspace_dim(k: int, p: int) -> int:

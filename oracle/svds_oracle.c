@@ -422,42 +422,63 @@ static double orc_finish_vector(orc_lanczos *L, double *w, int64_t len, double *
 
 /* nu <- estimates of v_{i+1}^T v_l, l = 1..i (i 1-based); returns 1 when
  * v_{i+1} must be re-orthogonalized. */
-static int orc_pr_nu(orc_lanczos *L, int64_t i, double beta)
+/* One step of each recurrence on plain arrays (T column-major, leading
+ * dimension ldt; mu, nu of length >= i + 2; anorm the ||A|| estimate).
+ * Returns the largest new estimate, or -1 when the norm is unusable. */
+double orc_pr_nu_step(int64_t i, const double *T, int64_t ldt, const double *mu, double *nu,
+                      double beta, double anorm)
 {
-    if (!(beta > 0.0) || !isfinite(beta)) return 1;
-    const double tau = ORC_PR_EPS * L->anorm / beta;
-    const double alpha_i = T_(L, i - 1, i - 1);
+    if (!(beta > 0.0) || !isfinite(beta)) return -1.0;
+    const double tau = ORC_PR_EPS * anorm / beta;
+    const double alpha_i = T[(i - 1) + (i - 1) * ldt];
     double mx = 0.0;
     for (int64_t l = 1; l <= i; l++) {
         double s = 0.0;
-        for (int64_t r = 1; r <= l; r++) s += T_(L, r - 1, l - 1) * L->mu[r - 1];
-        double x = (s - alpha_i * L->nu[l - 1]) / beta;
+        for (int64_t r = 1; r <= l; r++) s += T[(r - 1) + (l - 1) * ldt] * mu[r - 1];
+        double x = (s - alpha_i * nu[l - 1]) / beta;
         x += (x >= 0.0) ? tau : -tau;
-        L->nu[l - 1] = x;
+        nu[l - 1] = x;
         if (fabs(x) > mx) mx = fabs(x);
     }
-    L->nu[i] = 1.0;
-    return (mx > ORC_PR_DELTA) || L->force_v;
+    nu[i] = 1.0;
+    return mx;
 }
 
 /* mu <- estimates of u_{i+1}^T u_l, l = 1..i, from nu (v_{i+1}^T v_r,
- * r = 1..i+1); returns 1 when u_{i+1} must be re-orthogonalized. */
-static int orc_pr_mu(orc_lanczos *L, int64_t i, double alpha)
+ * r = 1..i+1) and the previous mu (u_i^T u_l). */
+double orc_pr_mu_step(int64_t i, const double *T, int64_t ldt, double *mu, const double *nu,
+                      double alpha, double anorm)
 {
-    if (!(alpha > 0.0) || !isfinite(alpha)) return 1;
-    const double tau = ORC_PR_EPS * L->anorm / alpha;
-    const double beta_i = T_(L, i - 1, i);
+    if (!(alpha > 0.0) || !isfinite(alpha)) return -1.0;
+    const double tau = ORC_PR_EPS * anorm / alpha;
+    const double beta_i = T[(i - 1) + i * ldt];
     double mx = 0.0;
     for (int64_t l = 1; l <= i; l++) {
         double s = 0.0;
-        for (int64_t r = l; r <= i + 1; r++) s += T_(L, l - 1, r - 1) * L->nu[r - 1];
-        double x = (s - beta_i * L->mu[l - 1]) / alpha;
+        for (int64_t r = l; r <= i + 1; r++) s += T[(l - 1) + (r - 1) * ldt] * nu[r - 1];
+        double x = (s - beta_i * mu[l - 1]) / alpha;
         x += (x >= 0.0) ? tau : -tau;
-        L->mu[l - 1] = x;
+        mu[l - 1] = x;
         if (fabs(x) > mx) mx = fabs(x);
     }
-    L->mu[i] = 1.0;
-    return (mx > ORC_PR_DELTA) || L->force_u;
+    mu[i] = 1.0;
+    return mx;
+}
+
+/* nu <- estimates of v_{i+1}^T v_l, l = 1..i (i 1-based); returns 1 when
+ * v_{i+1} must be re-orthogonalized. */
+static int orc_pr_nu(orc_lanczos *L, int64_t i, double beta)
+{
+    const double mx = orc_pr_nu_step(i, L->T, L->t + 1, L->mu, L->nu, beta, L->anorm);
+    return (mx < 0.0) || (mx > ORC_PR_DELTA) || L->force_v;
+}
+
+/* mu <- estimates of u_{i+1}^T u_l; returns 1 when u_{i+1} must be
+ * re-orthogonalized. */
+static int orc_pr_mu(orc_lanczos *L, int64_t i, double alpha)
+{
+    const double mx = orc_pr_mu_step(i, L->T, L->t + 1, L->mu, L->nu, alpha, L->anorm);
+    return (mx < 0.0) || (mx > ORC_PR_DELTA) || L->force_u;
 }
 
 /* Re-orthogonalizes w against the first `ncols` columns of W when `need`,

@@ -201,3 +201,58 @@ def test_oracle_estimates_bound_the_true_inner_products(orc, case):
         assert np.all(true_mu <= 10 * mu + 1e-15), np.max(true_mu / (mu + 1e-300))
         # and they are estimates, not blanket bounds: within a few orders of the truth
         assert np.max(nu) < 1e6 * max(np.max(true_nu), 1e-16)
+
+
+def _lanczos_without_reorth(orc, A, v0, steps):
+    """Plain Lanczos bidiagonalization (no re-orthogonalization, numpy) with
+    the oracle's two recurrence steps run alongside; per step the true and
+    estimated largest inner products of the new v and u with their
+    predecessors."""
+    n, m = A.shape[1], A.shape[0]
+    T = np.zeros((steps + 3, steps + 3), order="F")
+    V, U = np.zeros((n, steps + 2)), np.zeros((m, steps + 2))
+    V[:, 0] = v0 / np.linalg.norm(v0)
+    u = A @ V[:, 0]
+    a = np.linalg.norm(u)
+    U[:, 0], T[0, 0] = u / a, a
+    mu, nu = np.zeros(steps + 3), np.zeros(steps + 3)
+    mu[0] = nu[0] = 1.0
+    anorm, out = a, []
+    for i in range(1, steps + 1):
+        w = A.T @ U[:, i - 1] - T[i - 1, i - 1] * V[:, i - 1]
+        b = np.linalg.norm(w)
+        anorm = max(anorm, b)
+        orc.pr_nu_step(i, T, mu, nu, b, anorm)
+        V[:, i], T[i - 1, i] = w / b, b
+        tv, ev = np.abs(V[:, :i].T @ V[:, i]).max(), np.abs(nu[:i]).max()
+        w = A @ V[:, i] - b * U[:, i - 1]
+        a = np.linalg.norm(w)
+        anorm = max(anorm, a)
+        orc.pr_mu_step(i, T, mu, nu, a, anorm)
+        U[:, i], T[i, i] = w / a, a
+        tu, eu = np.abs(U[:, :i].T @ U[:, i]).max(), np.abs(mu[:i]).max()
+        out.append((tv, ev, tu, eu))
+    return out
+
+
+@pytest.mark.parametrize("case", ["sparse", "decay"])
+def test_oracle_recurrence_tracks_lost_orthogonality(orc, case):
+    """While the vectors are still nearly orthogonal (the regime the scheme
+    works in), each step's estimates follow the true loss of orthogonality
+    within fixed factors both ways: a dropped term makes them fall behind, a
+    wrong sign makes them explode."""
+    if case == "sparse":
+        a = synth.workload_sparse_small()
+        A, v0 = a.to_dense(), synth.start_vector(1000, 1)
+    else:
+        d = synth.workload_dense_decay(3, 0.03)
+        A, v0 = d.a, synth.start_vector(300, 1)
+    rows = _lanczos_without_reorth(orc, A, v0, 40)
+    checked = 0
+    for tv, ev, tu, eu in rows:
+        if max(tv, tu) > 1e-6:
+            break
+        assert tv <= 10 * ev + 1e-15 and tu <= 10 * eu + 1e-15, (tv, ev, tu, eu)
+        assert ev <= 1e3 * max(tv, 1e-15) and eu <= 1e3 * max(tu, 1e-15), (tv, ev, tu, eu)
+        checked += 1
+    assert checked >= 3
