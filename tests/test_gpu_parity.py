@@ -343,3 +343,36 @@ def test_solve_both_restart_gemms(pkg, orc, gemm):
     ref = orc.svds(a, 12, 12, 1e-10, 100, v0=v0)
     assert r.info["converged"] == 1
     _compare(r, ref, 12)
+
+
+@pytest.mark.parametrize("t,k,gemm", [(448, 224, "tensor"), (512, 256, "fma")])
+def test_solve_at_the_size_limits(pkg, orc, t, k, gemm):
+    """The documented limits: t = 448 with the tensor-core restart GEMM (its
+    exactness bound), t = 512 and k = 256 with the FP64-FMA GEMM; one round
+    and one restart, against the oracle (singular values of the projected
+    matrix after the restart)."""
+    a = synth.csr_uniform(3000, 1200, 0.01, 17)
+    v0 = synth.start_vector(a.n, 6)
+    r = pkg.svds(a, k, t - k, 1e-10, 2, v0=v0, restart_gemm=gemm)
+    ref = orc.svds(a, k, t - k, 1e-10, 2, v0=v0)
+    assert r.info["t"] == t and r.info["restarts"] == ref["info"]["restarts"] == 1
+    # after two rounds the trailing Ritz values are not converged; a Ritz
+    # value's error is of order res^2 sigma_1 / gap, so two runs that differ
+    # by rounding agree to that, and to 1e-9 where the residual is small
+    res = np.maximum(r.res, ref["res"])
+    tol = 1e-9 * ref["S"] + 10.0 * res ** 2 * ref["S"][0]
+    assert np.all(np.abs(r.S - ref["S"]) <= tol), np.max(np.abs(r.S - ref["S"]) / tol)
+    conv = res < 1e-8
+    assert conv.sum() >= k // 2
+    np.testing.assert_allclose(r.S[conv], ref["S"][conv], rtol=1e-9)
+    np.testing.assert_allclose(r.V.T @ r.V, np.eye(k), atol=1e-11)
+
+
+def test_solve_rejects_beyond_the_limits(pkg):
+    a = synth.csr_uniform(3000, 1200, 0.01, 17)
+    with pytest.raises(pkg.SvdscError):
+        pkg.svds(a, 100, 349, 1e-10, 2)                      # t = 449 > 448 with the tensor GEMM
+    with pytest.raises(pkg.SvdscError):
+        pkg.svds(a, 100, 413, 1e-10, 2, restart_gemm="fma")  # t = 513 > 512
+    with pytest.raises(pkg.SvdscError):
+        pkg.svds(a, 257, 100, 1e-10, 2, restart_gemm="fma")  # k = 257 > 256
