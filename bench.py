@@ -82,6 +82,18 @@ def make_workload(name, scale):
     return A, k, p, tol, prec
 
 
+def arm_config(A, args, k, p, tol, prec, maxit, ws):
+    """The `config` object both arms print (the GPU arm and the reference arm)."""
+    cfg = describe(A, args.workload, k, p, tol, prec)
+    a_bytes = (12 * int(A.row_ptr[-1])) if hasattr(A, "row_ptr") else 8 * A.m * A.n
+    cfg["l2"] = ("inputs larger than L2 (no flush): the matrix alone exceeds 129 MB"
+                 if a_bytes > 129e6 else "small working set (L2-resident)")
+    cfg["maxit"] = maxit
+    cfg["reorth"] = args.reorth
+    cfg["parallelism"] = "replicas" if ws > 1 else "single-gpu"
+    return cfg
+
+
 def describe(A, name, k, p, tol, prec):
     d = {"workload": f"{name}: {getattr(A, 'name', '')}", "m": int(A.m), "n": int(A.n), "k": k, "p": p,
          "tol": tol, "precision": prec}
@@ -286,7 +298,8 @@ def run_reference(args, ws, rank):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(walls),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": describe(A, args.workload, k, p, tol, prec),
+           "data": "synthetic",
+           "config": arm_config(A, args, k, p, tol, prec, MAXIT.get(args.workload, 1000), ws),
            "cpu_baseline": {"value": v, "unit": "s", "cores": smp["threads"], "kind": "oracle",
                             "sample": (f"per step: first {smp['steps']} Lanczos vectors of the initial LBP, "
                                        f"a {smp['gemm_rows']}-row slice of the restart GEMM and one "
@@ -523,13 +536,7 @@ def main():
                 ref_fp64_s = time.perf_counter() - t0
                 ref_fp64.S = ref_fp64.S.cpu().numpy()
     v0 = synth.start_vector(A.n, 1)
-    cfg = describe(A, args.workload, k, p, tol, prec)
-    a_bytes = (12 * int(A.row_ptr[-1])) if hasattr(A, "row_ptr") else 8 * A.m * A.n
-    cfg["l2"] = "inputs larger than L2 (no flush): the matrix alone exceeds 129 MB" \
-        if a_bytes > 129e6 else "small working set (L2-resident)"
-    cfg["maxit"] = maxit
-    cfg["reorth"] = args.reorth
-    cfg["parallelism"] = "replicas" if ws > 1 else "single-gpu"
+    cfg = arm_config(A, args, k, p, tol, prec, maxit, ws)
 
     stream = torch.cuda.current_stream()
     # the headline is timed without per-launch events; a second, instrumented

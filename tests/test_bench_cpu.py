@@ -34,6 +34,11 @@ def test_reference_arm_single_process():
     assert d["impl"] == "reference" and d["higher_is_better"] is False and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the same config object the GPU arm prints for this workload
+    for key in ("workload", "m", "n", "k", "p", "tol", "precision", "nnz", "l2", "maxit", "reorth",
+                "parallelism"):
+        assert key in d["config"], key
+    assert d["config"]["parallelism"] == "single-gpu" and d["config"]["reorth"] == "full"
 
 
 def test_reference_arm_two_gloo_ranks():
