@@ -1,7 +1,8 @@
 // Full re-orthogonalization (Sec. 2.1 of the svds-C paper) as CGS2 on the
 // device: h = W^T w (GEMV-T, per-CTA partial sums over row chunks + an ordered
 // reduction), w -= W h (GEMV-N, fused with the partial sums of ||w||^2 on the
-// last pass), then the norm / breakdown test / scaling of Alg. 1.
+// last pass), then the norm / breakdown test / scaling of Alg. 1; and the
+// estimate-driven gate of the optional partial re-orthogonalization.
 // Every reduction runs in a fixed order, so results are bitwise reproducible.
 #include <cstdint>
 #include <cstdio>
