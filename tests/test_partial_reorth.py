@@ -256,3 +256,35 @@ def test_oracle_recurrence_tracks_lost_orthogonality(orc, case):
         assert ev <= 1e3 * max(tv, 1e-15) and eu <= 1e3 * max(tu, 1e-15), (tv, ev, tu, eu)
         checked += 1
     assert checked >= 3
+
+
+def _low_rank(rank, m=120, n=90, seed=12):
+    rng = np.random.default_rng(seed)
+    X, Y = rng.standard_normal((m, rank)), rng.standard_normal((n, rank))
+    return X @ Y.T
+
+
+def test_oracle_partial_with_breakdowns(orc):
+    """A rank-6 matrix exhausts its Krylov space: breakdowns are repaired by
+    fresh orthogonalized vectors (estimates reset), and the singular values
+    are those of the full scheme / LAPACK."""
+    A = _low_rank(6)
+    s = np.linalg.svd(A, compute_uv=False)
+    r = orc.svds(A, 8, 12, 1e-10, 30, seed=1, reorth="partial", return_basis=True)
+    assert r["info"]["breakdowns"] > 0
+    np.testing.assert_allclose(r["S"][:6], s[:6], rtol=1e-12)
+    assert np.all(r["S"][6:] < 1e-12 * s[0])
+    assert _orth_loss(r["Vb"][:, :-1]) < ORTH
+
+
+@pytest.mark.gpu
+def test_gpu_partial_with_breakdowns(pkg, orc):
+    A = _low_rank(6)
+    s = np.linalg.svd(A, compute_uv=False)
+    r = pkg.svds(A, 8, 12, 1e-10, 30, seed=1, reorth="partial")
+    ref = orc.svds(A, 8, 12, 1e-10, 30, seed=1, reorth="partial")
+    assert r.info["breakdowns"] > 0
+    np.testing.assert_allclose(r.S[:6], s[:6], rtol=1e-12)
+    np.testing.assert_allclose(r.S[:6], ref["S"][:6], rtol=1e-12)
+    assert np.all(r.S[6:] < 1e-12 * s[0])
+    assert _orth_loss(r.V[:, :6]) < ORTH
