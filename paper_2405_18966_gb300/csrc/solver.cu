@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <vector>
+#include <nvtx3/nvToolsExt.h>
 #include "internal.cuh"
 
 using namespace svdsc;
@@ -119,6 +120,12 @@ static void ph_reset(svdsc_ctx *c)
         cudaError_t e_ = (x);                          \
         if (e_ != cudaSuccess) return SVDSC_ERR_CUDA;  \
     } while (0)
+
+// Named ranges for Nsight Systems timelines (no-ops unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 static inline double *colU(svdsc_ctx *c, int j) { return c->U + (int64_t)j * c->ldu; }
 static inline double *colV(svdsc_ctx *c, int j) { return c->V + (int64_t)j * c->ldv; }
@@ -561,6 +568,7 @@ static int issue_u(svdsc_ctx *c, int i)
 // iteration s starts with its u half (the v half was already formed).
 static int issue_segment(svdsc_ctx *c, int s, bool first_u)
 {
+    NvtxRange range("svdsc: Lanczos segment");
     for (int i = s; i <= c->t; i++) {
         if (!(first_u && i == s)) {
             int rc = issue_v(c, i);
@@ -674,6 +682,7 @@ int svdsc_destroy(svdsc_ctx *c)
 
 int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *opt, void *stream)
 {
+    NvtxRange range("svdsc_create");
     if (!out || !A) return SVDSC_ERR_ARG;
     *out = nullptr;
     if (A->m < 1 || A->n < 1) return SVDSC_ERR_ARG;
@@ -767,6 +776,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
                 double *S, double *U, int64_t ldu, double *V, int64_t ldv, double *res,
                 int out_on_device, svdsc_info *info)
 {
+    NvtxRange range("svdsc_solve");
     if (!c || k < 1 || !(tol > 0.0) || maxit < 1 || !S || !U || !V) return SVDSC_ERR_ARG;
     if (ldu < c->m || ldv < c->n) return SVDSC_ERR_ARG;
     const int t = (p < 0) ? std::max(15, 3 * k) : k + p;
@@ -839,6 +849,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         // Alg. 2: SVD of T(1:t,1:t)
         {
             const int e0 = ph_begin(c);
+            NvtxRange range("svdsc: projected SVD");
             CU(small_svd(t, c->T, t + 1, c->Sh, c->Uh, c->Vh, c->svd, c->st, s, nullptr));
             int nl = 1;
             if (c->which == SVDSC_SMALLEST) {  // wanted (smallest) triplets first, ascending
@@ -861,6 +872,8 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         if (c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
         if (c->st_host->converged || it == maxit) break;
         // augmented restart (Eq. 5-7)
+        {
+        NvtxRange restart_range("svdsc: augmented restart");
         if (c->restart_gemm == 0) {
             // U~_k = U(:,1:t) Uh(:,1:k), V~_k = V(:,1:t) Vh(:,1:k) into the other bases
             rc = gemm_tc(c, c->U, c->U32, c->ldu, c->m, t, c->Uh, k, c->Ua, c->U32a);
@@ -908,6 +921,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         cgs2(c, c->U, c->U32, c->ldu, k, colU(c, k), c->cm, poison_ptr(c));
         do_finalize(c, 0, k, Tent(c, k, k), 0);
         restarts++;
+        }
         // continue Alg. 1 from i = k+1
         rc = issue_segment(c, k + 1, false);
         if (rc) return rc;
@@ -917,6 +931,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     const DevStatus fin = *c->st_host;
 
     // outputs of Alg. 2 (into the spare bases or in place, then copied out)
+    NvtxRange out_range("svdsc: outputs");
     double *Uo = c->U, *Vo = c->V;
     if (c->restart_gemm == 0) {
         rc = gemm_tc(c, c->U, c->U32, c->ldu, c->m, t, c->Uh, k, c->Ua, nullptr);
