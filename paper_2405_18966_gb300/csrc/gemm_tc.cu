@@ -609,13 +609,10 @@ static cudaError_t launch_tc(const WT *W, int64_t ldw, int64_t rows, int t, cons
                              cudaStream_t s)
 {
     using Cfg = TileCfg<S, NT>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<S, NT, OZAKI, WT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::smem_bytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    cudaError_t e = set_smem_limit_once((const void *)tc_gemm_kernel<S, NT, OZAKI, WT>, Cfg::smem_bytes,
+                                        &attr_done);
+    if (e != cudaSuccess) return e;
     const int nchunks = (t + kKC - 1) / kKC;
     const int ncb = (k + NT - 1) / NT;
     dim3 pg((unsigned)((ncb * NT + 127) / 128), (unsigned)nchunks);

@@ -1,5 +1,6 @@
 // Internal declarations shared by the svdsc CUDA translation units.
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "../../include/svdsc.h"
@@ -52,7 +53,22 @@ struct PrState {
     int n_reorth;  // vectors the estimates sent to CGS2 in this solve
 };
 
-// Row chunking of one vector length for the row-blocked kernels.
+// Raises a kernel's dynamic shared-memory limit once per device (function
+// attributes belong to the device's context, so a process-wide flag would
+// skip the second GPU); thread-safe.
+inline cudaError_t set_smem_limit_once(const void *fn, int bytes, std::atomic<unsigned long long> *done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done->load() & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done->fetch_or(bit);
+    return e;
+}
+
+// Row chunking of one vector length for the row-blocked kernels.// Row chunking of one vector length for the row-blocked kernels.
 struct Chunk {
     int64_t len = 0;
     int64_t R = 0;   // rows per CTA (multiple of 64)

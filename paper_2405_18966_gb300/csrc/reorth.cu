@@ -130,12 +130,9 @@ void proj_partial(const double *W, int64_t ld, int ncols, const double *w, const
 {
     if (ncols <= 0) return;
     const size_t smem = sizeof(double) * (((c.R + 1) & ~int64_t(1)) + 32 * (size_t)ncols);
-    static size_t attr = 0;
-    if (smem > 48 * 1024 && smem > attr) {
-        // up to 4,096 rows of w plus 32 partials for up to 513 columns: < 170 KB
-        cudaFuncSetAttribute(proj_partial_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = 200 * 1024;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    if (smem > 48 * 1024)  // up to 4,096 rows of w plus 32 partials for up to 513 columns: < 170 KB
+        set_smem_limit_once((const void *)proj_partial_kernel<double>, 200 * 1024, &attr_done);
     proj_partial_kernel<double><<<c.nb, kProjWarps * 32, smem, s>>>(W, ld, ncols, w, c.len, c.R, c.nb, P, poison);
 }
 

@@ -431,13 +431,9 @@ cudaError_t small_svd(int t, const double *T, int64_t ldt, double *S, double *Uh
 {
     if (t <= kSmallT) {
         const size_t smem = 2 * sizeof(double) * kSmallT * kSmallT;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(jacobi_small_kernel,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        static std::atomic<unsigned long long> attr_done{0};
+        cudaError_t e = set_smem_limit_once((const void *)jacobi_small_kernel, (int)smem, &attr_done);
+        if (e != cudaSuccess) return e;
         jacobi_small_kernel<<<1, kSmallThreads, smem, s>>>(t, T, ldt, S, Uh, Vh, st, 100);
         if (launches) (*launches)++;
         return cudaGetLastError();

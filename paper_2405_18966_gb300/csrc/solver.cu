@@ -263,12 +263,8 @@ static int gemm_inplace(svdsc_ctx *c, double *W, int64_t ld, int64_t rows, int t
     const int max_doubles = (200 * 1024) / 8;
     if ((int64_t)KC * k > max_doubles) KC = std::max(1, max_doubles / k);
     const size_t smem = sizeof(double) * (size_t)KC * k;
-    static size_t attr = 0;
-    if (smem > 48 * 1024 && smem > attr) {
-        CU(cudaFuncSetAttribute(gemm_inplace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                200 * 1024));
-        attr = 200 * 1024;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    if (smem > 48 * 1024) CU(set_smem_limit_once((const void *)gemm_inplace_kernel, 200 * 1024, &attr_done));
     const int64_t blocks = std::min<int64_t>((rows + 31) / 32, 152 * (smem > 100 * 1024 ? 1 : 2));
     const int e0 = ph_begin(c);
     gemm_inplace_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), kGemmGroups * 32, smem, c->stream>>>(
