@@ -7,8 +7,11 @@
  * method is the one Sec. 2.1 describes: Lanczos bidiagonalization (Alg. 1) with
  * full re-orthogonalization of every new vector (here: two classical
  * Gram-Schmidt passes, "CGS2"), the Ritz residual test of Eq. (4), and the
- * augmented restart of Eq. (5)-(7) / Alg. 2.  Every step runs in this
- * library's CUDA kernels on the device; there is no CPU fallback.
+ * augmented restart of Eq. (5)-(7) / Alg. 2.  Options (svdsc_options): the
+ * k smallest triplets instead, partial re-orthogonalization instead of the
+ * full one, and a mixed-precision form; a batched form solves many matrices
+ * in one launch.  Every step runs in this library's CUDA kernels on the
+ * device; there is no CPU fallback.
  *
  * Conventions for every entry point:
  *   - Dense matrices are column-major with a leading dimension (the paper's
