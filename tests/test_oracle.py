@@ -325,3 +325,29 @@ def test_sign_rule(orc):
     np.testing.assert_array_equal(V2[:, 0], [-0.1, 0.5])
     np.testing.assert_array_equal(U2[:, 0], [-1.0, -3.0])
     np.testing.assert_array_equal(V2[:, 1], [0.9, -0.2])
+
+
+def test_oracle_dense_and_csr_forms_agree(orc):
+    """The same matrix as dense column-major and as CSR: same restarts and
+    singular values to rounding (the two product loops differ only in order)."""
+    a = synth.workload_sparse_small()
+    d = a.to_dense()
+    v0 = synth.start_vector(a.n, 1)
+    r1 = orc.svds(a, 8, 12, 1e-10, 100, v0=v0)
+    r2 = orc.svds(d, 8, 12, 1e-10, 100, v0=v0)
+    assert r1["info"]["restarts"] == r2["info"]["restarts"]
+    np.testing.assert_allclose(r1["S"], r2["S"], rtol=1e-13)
+    assert np.all(np.abs(np.sum(r1["V"] * r2["V"], axis=0)) > 1 - 1e-10)
+
+
+def test_oracle_transpose_swaps_the_factors(orc):
+    """svds(A^T) gives the singular values of svds(A), with U and V swapped
+    (A^T has the same singular values; its products are A's, exchanged)."""
+    a = synth.workload_sparse_small()
+    d = a.to_dense()
+    r = orc.svds(d, 6, 14, 1e-12, 200, seed=3)
+    rt = orc.svds(np.ascontiguousarray(d.T), 6, 14, 1e-12, 200, seed=3)
+    assert r["info"]["converged"] == 1 and rt["info"]["converged"] == 1
+    np.testing.assert_allclose(rt["S"], r["S"], rtol=1e-12)
+    assert np.all(np.abs(np.sum(rt["U"] * r["V"], axis=0)) > 1 - 1e-9)
+    assert np.all(np.abs(np.sum(rt["V"] * r["U"], axis=0)) > 1 - 1e-9)
