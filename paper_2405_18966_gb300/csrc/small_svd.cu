@@ -5,7 +5,8 @@
 // in round-robin (circle) order so that t/2 disjoint rotations run at once:
 //   t <= 64 : one CTA, B and V in shared memory, one warp per pair;
 //   t  > 64 : a cooperative multi-CTA kernel (one pair per CTA per round,
-//             B and V in global memory, bounded grid barrier between rounds),
+//             B and V in global memory, rounds ordered by per-column flags,
+//             one bounded grid barrier per sweep),
 // since GB300 has ~2 FP64 FMA/clk/SM and an O(t^3) sweep must be spread over
 // many SMs.  The convergence test matches the CPU oracle's:
 // |b_p . b_q| <= eps sqrt(t) ||b_p|| ||b_q||.
@@ -251,8 +252,11 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
                    double *sig, int *rot, unsigned *bar, DevStatus *st, int max_sweeps,
                    double *__restrict__ S, double *__restrict__ Uh, double *__restrict__ Vh)
 {
-    __shared__ double red[3][kCoopThreads / 32];
-    __shared__ double sv[3];
+    __shared__ double red[kCoopThreads / 32];
+    __shared__ double sv;
+    __shared__ double part[3][kCoopThreads];
+    __shared__ double s_cs[2];
+    __shared__ int s_rot;
     const unsigned nblk = gridDim.x;
     int *timeout = &st->timeout;
     // B = T, W = I
@@ -265,6 +269,7 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
     if (!grid_sync(bar, nblk, timeout)) return;
     const double tol = DBL_EPSILON * sqrt((double)t);
     const int n2 = t + (t & 1);
+    const int nwrow = t < kCoopThreads ? (t + 31) / 32 : kCoopThreads / 32;  // warps holding rows
     // Rounds are ordered by per-column version flags instead of grid
     // barriers: flag[c] counts the rounds completed on column c, the CTA that
     // owns the pair (p, q) in global round R waits (bounded) for both flags to
@@ -302,45 +307,73 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
                 double *bp = B + (int64_t)p * t, *bq = B + (int64_t)q * t;
                 double *wp = W + (int64_t)p * t, *wq = W + (int64_t)q * t;
                 // every element of both pairs of columns is loaded once, up front
-                // (t <= kCoopThreads * kCoopPer), and kept in registers
+                // (t <= kCoopThreads * kCoopPer), and kept in registers; warps
+                // past the last row skip the FP64 work
                 double xb[kCoopPer], yb[kCoopPer], xw[kCoopPer], yw[kCoopPer];
-                double a = 0.0, b = 0.0, g = 0.0;
 #pragma unroll
                 for (int u = 0; u < kCoopPer; u++) {
                     const int r = threadIdx.x + u * kCoopThreads;
-                    xb[u] = r < t ? __ldcg(bp + r) : 0.0;
-                    yb[u] = r < t ? __ldcg(bq + r) : 0.0;
-                    xw[u] = r < t ? __ldcg(wp + r) : 0.0;
-                    yw[u] = r < t ? __ldcg(wq + r) : 0.0;
+                    xb[u] = yb[u] = xw[u] = yw[u] = 0.0;
+                    if (r < t) {
+                        xb[u] = __ldcg(bp + r);
+                        yb[u] = __ldcg(bq + r);
+                        xw[u] = __ldcg(wp + r);
+                        yw[u] = __ldcg(wq + r);
+                    }
                 }
+                double a = 0.0, b = 0.0, g = 0.0;
 #pragma unroll
                 for (int u = 0; u < kCoopPer; u++) {
-                    a += xb[u] * xb[u];
-                    b += yb[u] * yb[u];
-                    g += xb[u] * yb[u];
+                    if (threadIdx.x + u * kCoopThreads < t) {
+                        a += xb[u] * xb[u];
+                        b += yb[u] * yb[u];
+                        g += xb[u] * yb[u];
+                    }
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    b += __shfl_xor_sync(0xffffffffu, b, o);
-                    g += __shfl_xor_sync(0xffffffffu, g, o);
-                }
-                if ((threadIdx.x & 31) == 0) {
-                    red[0][threadIdx.x >> 5] = a;
-                    red[1][threadIdx.x >> 5] = b;
-                    red[2][threadIdx.x >> 5] = g;
+                // GB300 issues FP64 at ~2 lanes/clk/SM, so the reduction and
+                // the rotation are done by one warp, not by every warp of the
+                // CTA: per-thread partials go through shared memory, warp 0
+                // adds them up and reduces the three sums with one transposed
+                // butterfly (6 FP64 adds instead of 3 x 5 per warp), and one
+                // lane computes the rotation.
+                part[0][threadIdx.x] = a;
+                part[1][threadIdx.x] = b;
+                part[2][threadIdx.x] = g;
+                __syncthreads();
+                if (threadIdx.x < 32) {
+                    const int lane = threadIdx.x;
+                    double v0 = part[0][lane], v1 = part[1][lane], v2 = part[2][lane];
+                    for (int w = 1; w < nwrow; w++) {
+                        v0 += part[0][lane + 32 * w];
+                        v1 += part[1][lane + 32 * w];
+                        v2 += part[2][lane + 32 * w];
+                    }
+                    // lanes with bit 4 clear gather (v0, v1), the others (v2, 0)
+                    const bool h16 = (lane & 16) != 0;
+                    double k0 = h16 ? v2 : v0, k1 = h16 ? 0.0 : v1;
+                    const double s0 = h16 ? v0 : v2, s1 = h16 ? v1 : 0.0;
+                    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+                    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+                    // bit 3 clear keeps the first of the two, set the second
+                    const bool h8 = (lane & 8) != 0;
+                    double k = h8 ? k1 : k0;
+                    k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+                    for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+                    // lane 0: sum of v0 (alpha), lane 8: v1 (beta), lane 16: v2 (gamma)
+                    const double beta = __shfl_sync(0xffffffffu, k, 8);
+                    const double gamma = __shfl_sync(0xffffffffu, k, 16);
+                    if (lane == 0) {
+                        double c = 1.0, s = 0.0;
+                        const bool do_rot = jacobi_rotation(k, beta, gamma, tol, &c, &s);
+                        s_cs[0] = c;
+                        s_cs[1] = s;
+                        s_rot = do_rot;
+                        if (do_rot) atomicAdd(rot + sweeps, 1);
+                    }
                 }
                 __syncthreads();
-                if (threadIdx.x < 3) {
-                    double tsum = 0.0;
-                    for (int w = 0; w < kCoopThreads / 32; w++) tsum += red[threadIdx.x][w];
-                    sv[threadIdx.x] = tsum;
-                }
-                __syncthreads();
-                double c, s;
-                const bool do_rot = jacobi_rotation(sv[0], sv[1], sv[2], tol, &c, &s);
-                __syncthreads();
-                if (do_rot && threadIdx.x == 0) atomicAdd(rot + sweeps, 1);
-                if (do_rot) {
+                if (s_rot) {
+                    const double c = s_cs[0], s = s_cs[1];
 #pragma unroll
                     for (int u = 0; u < kCoopPer; u++) {
                         const int r = threadIdx.x + u * kCoopThreads;
@@ -372,7 +405,7 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
             const double x = __ldcg(bj + r);
             a += x * x;
         }
-        const double tot = block_sum_coop(a, red[0], &sv[0]);
+        const double tot = block_sum_coop(a, red, &sv);
         if (threadIdx.x == 0) __stcg(sig + j, sqrt(tot));
     }
     if (!grid_sync(bar, nblk, timeout)) return;
