@@ -276,7 +276,7 @@ int svdsc_gemm(svdsc_ctx *ctx, int mode, int64_t rows, int t, int k, const doubl
  * front (cudaMalloc can synchronize the device and can fail mid-run), and
  * hosts that only hand a library pre-allocated buffers.  The paper has no
  * counterpart; it exists only for such callers.
- *   Scratch: one file-scope __device__ array of 4.2 MB (525,824 doubles) that
+ *   Scratch: one file-scope __device__ array of 4.3 MB (532,992 doubles) that
  *   every GPU loading this library holds until the process exits.  Limits:
  *   ncols <= 512 and len <= 4,194,304 (at most 1,024 row chunks of 4,096);
  *   larger sizes return SVDSC_ERR_SIZE before any GPU work.

@@ -68,11 +68,18 @@ inline cudaError_t set_smem_limit_once(const void *fn, int bytes, std::atomic<un
     return e;
 }
 
-// Row chunking of one vector length for the row-blocked kernels.// Row chunking of one vector length for the row-blocked kernels.
+// Row chunking of one vector length for the row-blocked kernels.
 struct Chunk {
     int64_t len = 0;
     int64_t R = 0;   // rows per CTA (multiple of 64)
     int nb = 0;      // number of CTAs
+    // layout of the FP64 GEMV-N (w -= W h), which also fixes the partial sums
+    // of ||w||^2: nbu CTAs of thu threads, Ru rows each.  Every producer
+    // (GEMV-N, norm_partial) and consumer (finalize, the estimate gate) of
+    // those partials uses nbu, so the norm is summed in one fixed order.
+    int64_t Ru = 0;
+    int nbu = 0;
+    int thu = 0;
 };
 Chunk make_chunk(int64_t len, int target_blocks);
 
@@ -113,6 +120,8 @@ struct DevDense {
 
 constexpr int kSpmvThreads = 256;
 constexpr int kRowThreads = 512;
+constexpr int kUpdSmallThreads = 256;               // FP64 GEMV-N small-CTA layout
+constexpr int64_t kUpdSmallMinRows = 1336 * 512;    // rows from which it is used
 
 // ---- products (spmv.cu)
 // y = A x - coef * z (z may be null; coef from *coef_dev when non-null, else coef_h)

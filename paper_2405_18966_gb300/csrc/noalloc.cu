@@ -17,11 +17,12 @@ namespace svdsc {
 
 constexpr int64_t kNoAllocMaxCols = 512;   // ncols limit
 constexpr int kNoAllocMaxChunks = 1024;    // row chunks of <= 4096 rows: len <= 4,194,304
+constexpr int kNoAllocMaxNormParts = 8192; // GEMV-N CTAs of >= 512 rows at that length
 constexpr size_t kNoAllocDoubles =
-    (size_t)kNoAllocMaxChunks * kNoAllocMaxCols + kNoAllocMaxCols + kNoAllocMaxChunks;
+    (size_t)kNoAllocMaxChunks * kNoAllocMaxCols + kNoAllocMaxCols + kNoAllocMaxNormParts;
 constexpr int kNoAllocMaxDevices = 64;
 
-// 4.2 MB of scratch per device: P (ncols x chunks), h (ncols), Pn (chunks).
+// 4.3 MB of scratch per device: P (ncols x chunks), h (ncols), Pn (GEMV-N CTAs).
 static __device__ __align__(256) double g_cgs2_scratch[kNoAllocDoubles];
 
 static std::mutex g_scratch_mu;
@@ -71,7 +72,7 @@ extern "C" int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, i
     if (((uintptr_t)W & 15) || ((uintptr_t)w & 15) || (ncols > 0 && (ldw & 1))) return SVDSC_ERR_ARG;
     if (ncols > kNoAllocMaxCols) return SVDSC_ERR_SIZE;
     const Chunk ch = make_chunk(len, 2 * 152);
-    if (ch.nb > kNoAllocMaxChunks) return SVDSC_ERR_SIZE;
+    if (ch.nb > kNoAllocMaxChunks || ch.nbu > kNoAllocMaxNormParts) return SVDSC_ERR_SIZE;
     double *base = nullptr;
     int rc = scratch_address(&base);
     if (rc != SVDSC_OK) return rc;
@@ -90,6 +91,6 @@ extern "C" int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, i
     } else {
         norm_partial(w, ch, Pn, nullptr, s);
     }
-    noalloc_norm_kernel<<<1, 256, 0, s>>>(Pn, ch.nb, norm_out);
+    noalloc_norm_kernel<<<1, 256, 0, s>>>(Pn, ch.nbu, norm_out);
     return cudaGetLastError() == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
 }

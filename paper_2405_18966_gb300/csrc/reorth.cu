@@ -21,6 +21,24 @@ Chunk make_chunk(int64_t len, int target_blocks)
     c.R = R;
     c.nb = (int)((len + R - 1) / R);
     if (c.nb < 1) c.nb = 1;
+    // FP64 GEMV-N: one 512-row pass per 256-thread CTA from 684,032 rows on
+    // (1.1 x 152 SMs x 8 CTAs x 512 rows); below that, the chunks above
+    // (about two CTAs per SM) keep the SMs evenly loaded.  Measured on GB300
+    // over 250,000 - 4,000,000 rows: small CTAs lose below ~one wave (500,000
+    // rows: 77 % of the FP64 FMA peak against 80 %) and win from 750,000 rows
+    // on (82-90 % against 58-84 %: the chunks' partial last pass and, past
+    // the 4,096-row cap, SMs holding one CTA more than the others).  A
+    // constant, not a query of the device, so the summation order of the
+    // norm never depends on it.
+    if (len >= kUpdSmallMinRows) {
+        c.Ru = 2 * kUpdSmallThreads;
+        c.thu = kUpdSmallThreads;
+    } else {
+        c.Ru = c.R;
+        c.thu = kRowThreads;
+    }
+    c.nbu = (int)((len + c.Ru - 1) / c.Ru);
+    if (c.nbu < 1) c.nbu = 1;
     return c;
 }
 
@@ -182,15 +200,13 @@ __device__ __forceinline__ double block_sum_256(double v, double *red)
 }
 
 // w(r) -= sum_c W(r, c) h(c) over chunk rows; Pn[b] = sum of the new w(r)^2
-template <typename WT>
-__global__ void __launch_bounds__(kRowThreads)
-update_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__restrict__ h,
-              double *__restrict__ w, int64_t len, int64_t R, double *__restrict__ Pn,
-              const int *poison)
+template <typename WT, int TH>
+__device__ __forceinline__ void update_body(const WT *__restrict__ W, int64_t ld, int ncols,
+                                            const double *__restrict__ h, double *__restrict__ w,
+                                            int64_t len, int64_t R, double *__restrict__ Pn)
 {
-    if (poisoned(poison)) return;
     extern __shared__ double hs[];
-    __shared__ double red[kRowThreads / 32];
+    __shared__ double red[TH / 32];
     float *hs32 = (float *)(hs + ncols);  // FP32 copy for the FP32 pass (converted once)
     for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
         hs[c] = h[c];
@@ -200,7 +216,7 @@ update_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__r
     const int64_t r0 = (int64_t)blockIdx.x * R;
     const int rows = (int)min(R, len - r0);
     double nrm = 0.0;
-    for (int j = 2 * threadIdx.x; j < rows; j += 2 * kRowThreads) {
+    for (int j = 2 * threadIdx.x; j < rows; j += 2 * TH) {
         const int64_t r = r0 + j;
         if (j + 1 < rows) {
             double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
@@ -279,12 +295,82 @@ update_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__r
     }
 }
 
+template <typename WT>
+__global__ void __launch_bounds__(kRowThreads)
+update_kernel(const WT *__restrict__ W, int64_t ld, int ncols, const double *__restrict__ h,
+              double *__restrict__ w, int64_t len, int64_t R, double *__restrict__ Pn,
+              const int *poison)
+{
+    if (poisoned(poison)) return;
+    update_body<WT, kRowThreads>(W, ld, ncols, h, w, len, R, Pn);
+}
+
+// The small-CTA layout of the FP64 GEMV-N, with the arithmetic of
+// update_kernel<double> written out: this body compiles to 40 registers (six
+// CTAs resident per SM), the shared template to 44 (five).  Asking for eight
+// CTAs (32 registers) spills and measured slower.
+__global__ void __launch_bounds__(kUpdSmallThreads)
+update_small_kernel(const double *__restrict__ W, int64_t ld, int ncols, const double *__restrict__ h,
+                    double *__restrict__ w, int64_t len, int64_t R, double *__restrict__ Pn,
+                    const int *poison)
+{
+    if (poisoned(poison)) return;
+    extern __shared__ double hs[];
+    __shared__ double red[kUpdSmallThreads / 32];
+    for (int c = threadIdx.x; c < ncols; c += kUpdSmallThreads) hs[c] = h[c];
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    const int rows = (int)min(R, len - r0);
+    double nrm = 0.0;
+    for (int j = 2 * threadIdx.x; j < rows; j += 2 * kUpdSmallThreads) {
+        const int64_t r = r0 + j;
+        if (j + 1 < rows) {
+            double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+            const double *p = W + r;
+            int c = 0;
+            for (; c + 1 < ncols; c += 2) {
+                const double2 v0 = __ldcs((const double2 *)(p + (int64_t)c * ld));
+                const double2 v1 = __ldcs((const double2 *)(p + (int64_t)(c + 1) * ld));
+                a0 = fma(v0.x, hs[c], a0);
+                a1 = fma(v0.y, hs[c], a1);
+                b0 = fma(v1.x, hs[c + 1], b0);
+                b1 = fma(v1.y, hs[c + 1], b1);
+            }
+            for (; c < ncols; c++) {
+                const double2 v0 = __ldcs((const double2 *)(p + (int64_t)c * ld));
+                a0 = fma(v0.x, hs[c], a0);
+                a1 = fma(v0.y, hs[c], a1);
+            }
+            const double n0 = w[r] - (a0 + b0);
+            const double n1 = w[r + 1] - (a1 + b1);
+            w[r] = n0;
+            w[r + 1] = n1;
+            nrm = fma(n0, n0, nrm);
+            nrm = fma(n1, n1, nrm);
+        } else {
+            double a0 = 0.0;
+            for (int c = 0; c < ncols; c++) a0 = fma(W[r + (int64_t)c * ld], hs[c], a0);
+            const double n0 = w[r] - a0;
+            w[r] = n0;
+            nrm = fma(n0, n0, nrm);
+        }
+    }
+    if (Pn) {
+        const double t = block_sum_256(nrm, red);
+        if (threadIdx.x == 0) Pn[blockIdx.x] = t;
+    }
+}
+
 void update_sub(const double *W, int64_t ld, int ncols, const double *h, double *w, const Chunk &c,
                 double *Pn, const int *poison, cudaStream_t s)
 {
     if (ncols <= 0 && !Pn) return;
-    update_kernel<double><<<c.nb, kRowThreads, sizeof(double) * (ncols > 0 ? ncols : 1), s>>>(
-        W, ld, ncols, h, w, c.len, c.R, Pn, poison);
+    const size_t smem = sizeof(double) * (ncols > 0 ? ncols : 1);
+    if (c.thu == kUpdSmallThreads)
+        update_small_kernel<<<c.nbu, kUpdSmallThreads, smem, s>>>(W, ld, ncols, h, w, c.len, c.Ru, Pn,
+                                                                  poison);
+    else
+        update_kernel<double><<<c.nbu, kRowThreads, smem, s>>>(W, ld, ncols, h, w, c.len, c.Ru, Pn, poison);
 }
 
 void update_sub_f32(const float *W32, int64_t ld, int ncols, const double *h, double *w,
@@ -311,7 +397,7 @@ norm_partial_kernel(const double *__restrict__ w, int64_t len, int64_t R, double
 
 void norm_partial(const double *w, const Chunk &c, double *Pn, const int *poison, cudaStream_t s)
 {
-    norm_partial_kernel<<<c.nb, kRowThreads, 0, s>>>(w, c.len, c.R, Pn, poison);
+    norm_partial_kernel<<<c.nbu, kRowThreads, 0, s>>>(w, c.len, c.Ru, Pn, poison);
 }
 
 // ---------------------------------------------------------------- finalize
@@ -359,7 +445,7 @@ finalize_kernel(double *__restrict__ w, int64_t len, int64_t R, const double *__
 void finalize(double *w, const Chunk &c, const double *Pn, double *T_entry, DevStatus *st, int step,
               int parity, int mode, float *w32, cudaStream_t s)
 {
-    finalize_kernel<<<c.nb, kRowThreads, 0, s>>>(w, c.len, c.R, Pn, c.nb, T_entry, st, step, parity,
+    finalize_kernel<<<c.nb, kRowThreads, 0, s>>>(w, c.len, c.R, Pn, c.nbu, T_entry, st, step, parity,
                                                  mode, w32);
 }
 
@@ -469,7 +555,7 @@ void pr_omega(int side, int i, int kk, const double *T, int ldt, double *mu, dou
               const double *Pn, const DevStatus *st, int parity, PrState *pr, double bt, double bn,
               double fl, cudaStream_t s)
 {
-    pr_omega_kernel<<<1, kRowThreads, 0, s>>>(side, i, kk, T, ldt, mu, nu, Pn, c.nb, st, parity, pr, bt,
+    pr_omega_kernel<<<1, kRowThreads, 0, s>>>(side, i, kk, T, ldt, mu, nu, Pn, c.nbu, st, parity, pr, bt,
                                               bn, fl);
 }
 

@@ -407,7 +407,7 @@ static int reserve_ws(svdsc_ctx *c, int t)
     alloc((void **)&c->mu, sizeof(double) * cols);
     alloc((void **)&c->nu, sizeof(double) * cols);
     alloc((void **)&c->pr, sizeof(PrState));
-    alloc((void **)&c->Pn, sizeof(double) * nbmax);
+    alloc((void **)&c->Pn, sizeof(double) * std::max({nbmax, c->cm.nbu, c->cn.nbu}));
     alloc((void **)&c->Sh, sizeof(double) * t);
     alloc((void **)&c->Uh, sizeof(double) * (size_t)t * t);
     alloc((void **)&c->Vh, sizeof(double) * (size_t)t * t);
@@ -1018,7 +1018,7 @@ int svdsc_cgs2(svdsc_ctx *c, int64_t len, int64_t ncols, const double *W, int64_
     if (!ch) return SVDSC_ERR_ARG;
     if (ncols > c->t_cap + 1) return SVDSC_ERR_SIZE;
     cgs2(c, W, nullptr, ldw, (int)ncols, w, *ch, nullptr);
-    sum_sqrt_kernel<<<1, 256, 0, c->stream>>>(c->Pn, ch->nb, norm_out);
+    sum_sqrt_kernel<<<1, 256, 0, c->stream>>>(c->Pn, ch->nbu, norm_out);
     if (cudaGetLastError() != cudaSuccess) return SVDSC_ERR_CUDA;
     return cudaStreamSynchronize(c->stream) == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
 }

@@ -122,6 +122,28 @@ def test_cgs2_vs_oracle(pkg, orc, torch_mod, ncols):
     assert abs(nrm - np.linalg.norm(ref)) <= 1e-13 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("ncols", [1, 33])
+def test_cgs2_vs_oracle_small_cta_layout(pkg, orc, torch_mod, ncols):
+    """From 684,032 rows on, the FP64 GEMV-N runs as one 512-row pass per
+    256-thread CTA and the norm partials follow that layout: 700,001 rows
+    (1,368 CTAs, the last one with a single odd row)."""
+    torch = torch_mod
+    m = 700_001
+    A = synth.csr_uniform(m, 300, 0.0002, 4)
+    rng = np.random.default_rng(100 + ncols)
+    W, _ = np.linalg.qr(rng.standard_normal((m, ncols)))
+    w = W @ rng.standard_normal(ncols) + 1e-3 * rng.standard_normal(m)
+    ref = orc.cgs2(W, w)
+    Wt = torch.zeros((ncols, m + 1), dtype=torch.float64, device="cuda")
+    Wt[:, :m] = torch.tensor(W.T, device="cuda")
+    with pkg.Solver(A) as s:
+        s.reserve(max(ncols, 2))
+        got, nrm = s.cgs2(Wt, torch.tensor(w, device="cuda"))
+    got = got.cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.linalg.norm(w))
+    assert abs(nrm - np.linalg.norm(ref)) <= 1e-13 * np.linalg.norm(ref)
+
+
 # ---------------------------------------------------------- projected SVD
 
 @pytest.mark.parametrize("t", [1, 2, 20, 63, 64, 65, 128, 201])

@@ -32,11 +32,11 @@ def _case(torch, m, ncols, seed):
     return Wt, torch.tensor(w, device="cuda"), np.linalg.norm(w)
 
 
-def test_noalloc_cgs2_matches_allocating_entry_point():
+@pytest.mark.parametrize("m", [90_001, 700_001])  # ragged tails; the second in the small-CTA GEMV-N layout
+def test_noalloc_cgs2_matches_allocating_entry_point(m):
     torch, pkg = _setup()
     L = pkg.lib()
-    m = 90_001  # several row chunks and a ragged tail
-    A = synth.csr_uniform(m, 300, 0.001, 3)
+    A = synth.csr_uniform(m, 300, 0.0002, 3)
     with pkg.Solver(A) as s:
         s.reserve(64)
         for call, (ncols, seed) in enumerate([(37, 1), (64, 2)]):  # two calls in a row
