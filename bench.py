@@ -33,7 +33,12 @@ HBM_NOMINAL_GBS = 7900.0
 # DRAM bytes (read + write) / algorithmic bytes of the top kernels, from the
 # full-size ncu captures summarised in
 # profiles/cgs2_gemv_pair_1000000x150_and_spmv_sell_zipf.md
-TRAFFIC_RATIO = {"gemv_t": 1210.89 / 1208.0, "gemv_n": 1214.24 / 1216.0, "spmv": 270.62 / 263.2}
+# ncu DRAM bytes / algorithmic bytes per kernel (1,000,000 x 150 GEMVs, full SpMV).
+# GEMV-N has two layouts: update_small_kernel on the 1,000,000-row side
+# (1,213.64 MB) and update_kernel on the 500,000-row side (1,214.24 MB at
+# 1,000,000 rows), weighted 2:1 by the rows they stream in the solve.
+TRAFFIC_RATIO = {"gemv_t": 1210.89 / 1208.0, "gemv_n": (2 * 1213.64 + 1214.24) / 3 / 1216.0,
+                 "spmv": 270.62 / 263.2}
 # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 

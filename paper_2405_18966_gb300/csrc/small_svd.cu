@@ -24,15 +24,35 @@ __device__ __forceinline__ void rr_pair(int slot, int round, int n2, int *p, int
     *q = a < b ? b : a;
 }
 
-// rotation of Golub & Van Loan (one-sided Jacobi): zeroes gamma in
-// [alpha gamma; gamma beta]; same formula as the oracle.
+// Rotation of Golub & Van Loan (one-sided Jacobi) that zeroes gamma in
+// [alpha gamma; gamma beta]; same skip test as the oracle.  With d = beta -
+// alpha and zeta = d / (2 gamma), tan = sign(zeta) / (|zeta| + sqrt(1 +
+// zeta^2)) is evaluated as sign(zeta) |2 gamma| / (|d| + sqrt(d^2 + 4
+// gamma^2)) (numerator and denominator times |2 gamma|) and c = rsqrt(1 +
+// tan^2): one square root, one division and one reciprocal square root on the
+// critical path instead of three square roots and three divisions, which on
+// GB300's narrow FP64 pipe are the longest part of a Jacobi round.  d and
+// 2 gamma are first scaled by an exact power of two so their squares cannot
+// overflow or lose everything to underflow.
 __device__ __forceinline__ bool jacobi_rotation(double alpha, double beta, double gamma, double tol,
                                                 double *c, double *s)
 {
     if (gamma == 0.0 || fabs(gamma) <= tol * sqrt(alpha * beta)) return false;
-    const double zeta = (beta - alpha) / (2.0 * gamma);
-    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    *c = 1.0 / sqrt(1.0 + tt * tt);
+    const double d = beta - alpha, g2 = 2.0 * gamma;
+    const double mx = fmax(fabs(d), fabs(g2));
+    if (!isfinite(mx)) return false;
+    // 2^-floor(log2 mx) from the exponent field (mx > 0: g2 != 0), clamped to
+    // the normal range: a subnormal mx (field 0) gets 2^1023, which brings it
+    // above 2^-52, and mx >= 2^1023 gets 2^-1022, which leaves it below 4
+    const int ex = (int)((unsigned long long)__double_as_longlong(mx) >> 52) & 0x7FF;
+    const int fs = ex == 0 ? 2046 : (ex >= 2046 ? 1 : 2046 - ex);
+    const double sc = __longlong_as_double((long long)fs << 52);
+    const double ds = d * sc, gs = fabs(g2) * sc;
+    const double r = sqrt(fma(ds, ds, gs * gs));
+    // sign(zeta), with zeta = +-0 counted as positive like the unscaled form
+    const bool neg = d != 0.0 && ((d > 0.0) != (gamma > 0.0));
+    const double tt = (neg ? -gs : gs) / (fabs(ds) + r);
+    *c = rsqrt(fma(tt, tt, 1.0));
     *s = *c * tt;
     return true;
 }
@@ -290,7 +310,12 @@ jacobi_coop_kernel(int t, const double *__restrict__ T, int64_t ldt, double *B, 
                 if (threadIdx.x == 0) {
                     int ok = 1;
                     unsigned long long spins = 0;
-                    while (ld_acquire_u32(flag + p) < R || (!idle && ld_acquire_u32(flag + q) < R)) {
+                    // both flags are loaded before either is tested: one L2
+                    // round trip per poll instead of two
+                    for (;;) {
+                        const unsigned fp = ld_acquire_u32(flag + p);
+                        const unsigned fq = idle ? R : ld_acquire_u32(flag + q);
+                        if (fp >= R && fq >= R) break;
                         if (++spins > (1ull << 24) || *(volatile int *)timeout) { ok = 0; break; }
                         if (spins > 256) __nanosleep(32);
                     }
