@@ -203,6 +203,26 @@ def test_solve_sparse_2000x1000(pkg, orc):
     assert np.all(r.res < 1e-10)
 
 
+@pytest.mark.parametrize("k,p", [(20, 20), (10, 30)])
+def test_solve_zipf_structure_vs_lapack(pkg, orc, k, p):
+    """The Zipf workload at 0.5 % scale (5,000 x 2,500): sigma against
+    LAPACK's dense SVD (a check only) and the oracle; vectors within the
+    Wedin bound of their gaps."""
+    a = synth.workload_sparse_zipf(0.005)
+    Ul, s, Vlt = np.linalg.svd(a.to_dense(), full_matrices=False)
+    v0 = synth.start_vector(a.n, 1)
+    r = pkg.svds(a, k, p, 1e-10, 500, v0=v0)
+    ref = orc.svds(a, k, p, 1e-10, 500, v0=v0)
+    assert r.status == pkg.OK and r.info["converged"] == 1
+    assert abs(r.info["restarts"] - ref["info"]["restarts"]) <= 1
+    np.testing.assert_allclose(r.S, s[:k], rtol=1e-12)
+    np.testing.assert_allclose(r.S, ref["S"], rtol=1e-12)
+    gaps = np.minimum(np.abs(s[:k] - s[1:k + 1]), np.abs(s[:k] - np.r_[np.inf, s[:k - 1]]))
+    bound = 10 * 1e-10 * s[:k] / gaps + 1e-12
+    assert np.all(_sin_angles(r.V, Vlt[:k].T) <= bound)
+    assert np.all(_sin_angles(r.U, Ul[:, :k]) <= bound)
+
+
 def test_solve_random_start_matches_oracle_rng(pkg, orc):
     """No v0: both sides draw v_1 from the same counter-based generator."""
     a = synth.workload_sparse_small()

@@ -351,3 +351,26 @@ def test_oracle_transpose_swaps_the_factors(orc):
     np.testing.assert_allclose(rt["S"], r["S"], rtol=1e-12)
     assert np.all(np.abs(np.sum(rt["U"] * r["V"], axis=0)) > 1 - 1e-9)
     assert np.all(np.abs(np.sum(rt["V"] * r["U"], axis=0)) > 1 - 1e-9)
+
+
+@pytest.mark.parametrize("k,p", [(20, 20), (10, 30)])
+def test_oracle_zipf_structure_vs_lapack(orc, k, p):
+    """The Zipf workload's structure (Zipf(1.5) row lengths, 39 % one-entry
+    rows, heavy rows near the cap) at 0.5 % scale, 5,000 x 2,500: the k
+    largest singular values against LAPACK's dense SVD (a library routine, a
+    check only) and the vectors within the Wedin bound of their gaps."""
+    a = synth.workload_sparse_zipf(0.005)
+    ad = a.to_dense()
+    Ul, s, Vlt = np.linalg.svd(ad, full_matrices=False)
+    r = orc.svds(a, k, p, 1e-10, 500, v0=synth.start_vector(a.n, 1))
+    assert r["info"]["converged"] == 1 and r["info"]["restarts"] > 0
+    np.testing.assert_allclose(r["S"], s[:k], rtol=1e-13)
+    gaps = np.minimum(np.abs(s[:k] - s[1:k + 1]), np.abs(s[:k] - np.r_[np.inf, s[:k - 1]]))
+    bound = 10 * 1e-10 * s[:k] / gaps + 1e-12  # Wedin: residual / gap, with slack
+
+    def sines(X, Y):  # sine of the angle between matching columns, sign-free
+        c = np.sum(X * Y, axis=0)
+        return np.linalg.norm(Y - X * c, axis=0)
+
+    assert np.all(sines(Vlt[:k].T, r["V"]) <= bound)
+    assert np.all(sines(Ul[:, :k], r["U"]) <= bound)
