@@ -86,6 +86,9 @@ def lib():
             L.orc_svds.argtypes = [C.POINTER(_Mat), i64, i64, dbl, i64, i64, i64, C.c_uint64, vp, i64,
                                    vp, vp, i64, vp, i64, vp, C.POINTER(Info), vp, vp, vp, vp, vp]
             L.orc_svds.restype = C.c_int
+            L.orc_svds_block.argtypes = [C.POINTER(_Mat), i64, i64, i64, dbl, i64, C.c_uint64, vp, vp, vp,
+                                         i64, vp, i64, vp, C.POINTER(Info), vp, vp, vp, vp]
+            L.orc_svds_block.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             for f in ("orc_pr_nu_step", "orc_pr_mu_step"):
                 getattr(L, f).argtypes = [i64, vp, i64, vp, vp, dbl, dbl]
@@ -283,4 +286,52 @@ def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, seed: int
     out = {"S": S, "U": U, "V": V, "res": res, "info": info.as_dict(), "t": t}
     if return_basis:
         out.update(Ub=Ub, Vb=Vb, T=Tb, mu=mu, nu=nu)
+    return out
+
+
+def block_sizes(k: int, p: int, b: int):
+    """(t0, t1): projected sizes of the block form's first pass and of every
+    pass after a restart (t = k + p rounded up to whole blocks)."""
+    t = subspace_dim(k, p)
+    return b * (-(-t // b)), k + b * (-(-(t - k) // b))
+
+
+def svds_block(A, k: int, p: int = -1, b: int = 1, tol: float = 1e-10, maxit: int = 100,
+               seed: int = 0, V0=None, return_basis: bool = False):
+    """Block form of Alg. 2 (block Lanczos bidiagonalization, block size b, full
+    re-orthogonalization, augmented restart); b = 1 is the single-vector form.
+    V0: n x b start block or None (draws 0..b-1).  Returns the dict of svds
+    (S, U, V, res, info) plus t_last (size of the last projected matrix) and,
+    with return_basis, Ub (m x tmax), Vb (n x (tmax + b)) and T
+    ((tmax + b) x (tmax + b)) of the last pass."""
+    if b < 1:
+        raise ValueError("block size b must be >= 1")
+    bd = _Bound(A)
+    m, n = bd.m, bd.n
+    t0, t1 = block_sizes(k, p, b)
+    tmax = max(t0, t1)
+    S = np.zeros(k)
+    U = np.zeros((m, k), order="F")
+    V = np.zeros((n, k), order="F")
+    res = np.zeros(k)
+    info = Info()
+    v0a = None if V0 is None else np.asfortranarray(V0, dtype=np.float64).reshape(n, b, order="F")
+    Ub = Vb = Tb = None
+    if return_basis:
+        Ub = np.zeros((m, tmax), order="F")
+        Vb = np.zeros((n, tmax + b), order="F")
+        Tb = np.zeros((tmax + b, tmax + b), order="F")
+    tl = C.c_int64(0)
+    rc = lib().orc_svds_block(C.byref(bd.mat), k, p, b, tol, maxit, C.c_uint64(seed), _ptr(v0a),
+                              _ptr(S), _ptr(U), m, _ptr(V), n, _ptr(res), C.byref(info),
+                              _ptr(Ub), _ptr(Vb), _ptr(Tb), C.byref(tl))
+    if rc == -1:
+        raise ValueError("bad arguments (need b >= 1, k + b <= t1, max(t0, t1) <= m, "
+                         "max(t0, t1) + b <= n, tol > 0, maxit >= 1)")
+    if rc != 0:
+        raise MemoryError("oracle ran out of memory")
+    out = {"S": S, "U": U, "V": V, "res": res, "info": info.as_dict(), "t0": t0, "t1": t1,
+           "t_last": int(tl.value), "b": b}
+    if return_basis:
+        out.update(Ub=Ub, Vb=Vb, T=Tb)
     return out

@@ -734,3 +734,303 @@ int orc_svds(const orc_mat *A, int64_t k, int64_t p, double tol, int64_t maxit, 
     free(Uh); free(Vh); free(Sh); free(Tt); free(Uk); free(Vk); free(rho);
     return 0;
 }
+
+/* ================================================================ block form
+ *
+ * Block Lanczos bidiagonalization (Golub, Luk & Overton 1981) with the full
+ * re-orthogonalization of Sec. 2.1 and the augmented restart of Alg. 2,
+ * carried over from single vectors to blocks of b columns.  With b = 1 every
+ * step below is the single-vector step of orc_svds, in the same order.
+ *
+ * Blocks (column offsets c are multiples of b before the first restart and
+ * k + multiples of b after it):
+ *   V(:, 0:b)  = orthonormalized start block
+ *   U(:, 0:b) R = A V(:, 0:b)                          R -> T(0:b, 0:b)
+ *   repeat, with c = columns of U and V formed so far:
+ *     Z = A^T U(:, c-b:c) - V(:, c-b:c) T(c-b:c, c-b:c)^T
+ *     Z -> V(:, c:c+b) S      (S upper triangular)      S^T -> T(c-b:c, c:c+b)
+ *     stop here when c = t (V(:, t:t+b) is the residual block)
+ *     W = A V(:, c:c+b) - U(:, c-b:c) T(c-b:c, c:c+b)
+ *     W -> U(:, c:c+b) R                               R -> T(c:c+b, c:c+b)
+ * so that A V(:, 0:t) = U(:, 0:t) T(0:t, 0:t) and
+ * A^T U(:, 0:t) = V(:, 0:t) T(0:t, 0:t)^T + V(:, t:t+b) F^T E^T, with
+ * F = T(t-b:t, t:t+b) and E the last b columns of the identity: T is upper
+ * triangular with bandwidth b.  Each "->" is: both CGS passes of every column
+ * against the earlier blocks (coefficients discarded: they vanish in exact
+ * arithmetic), then a QR of the block column by column, each column
+ * projected twice against the block's earlier columns (coefficients summed
+ * into the triangular factor) and normalised.  A column whose norm falls to
+ * 1e-13 * (largest norm or sigma seen) has a zero diagonal entry and is
+ * replaced by a random vector orthogonalized (CGS2) against every earlier
+ * column of its basis, as a broken-down single vector is.
+ *
+ * Ritz triplets of T(0:t, 0:t) = Uh diag(sigma) Vh^T: the residual of Eq. (4)
+ * becomes res_j = || F^T Uh(t-b:t, j) ||_2 / sigma_j.  Augmented restart
+ * (Eq. 5-7 with a block): rho = Uh(t-b:t, 0:k)^T F (k x b);
+ * T <- [diag(sigma_1..k), rho; 0, R'] where U(:, k:k+b) R' comes from
+ * W = A V(:, k:k+b) - U~_k rho after V(:, k:k+b) := V(:, t:t+b).
+ * Subspace sizes: t0 = b * ceil(t / b) columns in the first pass and
+ * t1 = k + b * ceil((t - k) / b) after each restart (t = k + p); both equal
+ * t when b = 1.  Draws 0..b-1 are the start block's columns.
+ */
+typedef struct {
+    const orc_mat *A;
+    int64_t m, n, b, ld_t;  /* ld_t: leading dimension of T */
+    double *U, *V, *T;      /* U: m x tmax, V: n x (tmax + b), T: ld_t x ld_t */
+    double *h, *wm, *wn;    /* scratch: h (ld_t), wm (m x b), wn (n x b) */
+    uint64_t seed, draws;
+    double anorm;
+    orc_info *info;
+} orc_block;
+
+#define TB_(L, i, j) ((L)->T[(i) + (j) * (L)->ld_t])
+
+/* Orthonormalizes the len x b block Wb into columns c..c+b-1 of Basis (ld
+ * len): CGS2 of each column against Basis(:, 0:c), then the column-by-column
+ * QR; the triangular factor goes to R (b x b, leading dimension ldr). */
+static void orc_block_orth(orc_block *L, double *Wb, int64_t len, double *Basis, int64_t c,
+                           double *R, int64_t ldr)
+{
+    const int64_t b = L->b;
+    for (int64_t l = 0; l < b && c > 0; l++) {
+        double *w = Wb + l * len;
+        orc_cgs2(len, c, Basis, len, w, L->h);            /* against the earlier blocks */
+        L->info->n_reorth++;
+    }
+    for (int64_t l = 0; l < b; l++) {
+        double *w = Wb + l * len;
+        double *Q = Basis + c * len;                      /* the block's finished columns */
+        for (int64_t i = 0; i < b; i++) R[i + l * ldr] = 0.0;
+        for (int pass = 0; pass < 2; pass++) {
+            if (l == 0) break;
+            orc_gemv_t(len, l, Q, len, w, L->h);
+            orc_gemv_n_sub(len, l, Q, len, L->h, w);
+            for (int64_t i = 0; i < l; i++) R[i + l * ldr] += L->h[i];
+        }
+        double nrm = orc_norm2(len, w);
+        if (!(nrm > 1e-13 * L->anorm) || !isfinite(nrm)) {
+            L->info->breakdowns++;
+            R[l + l * ldr] = 0.0;
+            double *dst = Basis + (c + l) * len;
+            int ok = 0;
+            for (int attempt = 0; attempt < 8 && !ok; attempt++) {
+                orc_rng_vector(L->seed, L->draws++, len, w);
+                orc_cgs2(len, c + l, Basis, len, w, L->h);
+                double nr = orc_norm2(len, w);
+                if (nr > 1e-8) {
+                    for (int64_t r = 0; r < len; r++) dst[r] = w[r] / nr;
+                    ok = 1;
+                }
+            }
+            if (!ok)
+                for (int64_t r = 0; r < len; r++) dst[r] = 0.0;
+            continue;
+        }
+        if (nrm > L->anorm) L->anorm = nrm;
+        R[l + l * ldr] = nrm;
+        for (int64_t r = 0; r < len; r++) Basis[r + (c + l) * len] = w[r] / nrm;
+    }
+}
+
+/* Block Lanczos steps from c columns (c >= b; U and V hold c columns, the
+ * last U block's R in T) until V holds tc + b columns. */
+static void orc_block_lbp_from(orc_block *L, int64_t c, int64_t tc)
+{
+    const int64_t m = L->m, n = L->n, b = L->b;
+    for (;;) {
+        /* Z = A^T U(:, c-b:c) - V(:, c-b:c) T(c-b:c, c-b:c)^T */
+        for (int64_t l = 0; l < b; l++) {
+            double *z = L->wn + l * n;
+            orc_matvec_t(L->A, L->U + (c - b + l) * m, z);
+            L->info->n_matvec++;
+            /* column l of T(c-b:c, c-b:c)^T is row l of the block: T(c-b+l, c-b+i) */
+            for (int64_t i = 0; i < b; i++) {
+                const double coef = TB_(L, c - b + l, c - b + i);
+                if (coef == 0.0) continue;
+                const double *v = L->V + (c - b + i) * n;
+                for (int64_t r = 0; r < n; r++) z[r] -= coef * v[r];
+            }
+        }
+        double *S = L->h + L->ld_t;  /* b x b scratch after h */
+        orc_block_orth(L, L->wn, n, L->V, c, S, b);
+        for (int64_t i = 0; i < b; i++)           /* T(c-b:c, c:c+b) = S^T */
+            for (int64_t l = 0; l < b; l++) TB_(L, c - b + i, c + l) = S[l + i * b];
+        L->info->n_steps += b;
+        if (c >= tc) break;
+        /* W = A V(:, c:c+b) - U(:, c-b:c) T(c-b:c, c:c+b) */
+        for (int64_t l = 0; l < b; l++) {
+            double *w = L->wm + l * m;
+            orc_matvec(L->A, L->V + (c + l) * n, w);
+            L->info->n_matvec++;
+            for (int64_t i = 0; i < b; i++) {
+                const double coef = TB_(L, c - b + i, c + l);
+                if (coef == 0.0) continue;
+                const double *u = L->U + (c - b + i) * m;
+                for (int64_t r = 0; r < m; r++) w[r] -= coef * u[r];
+            }
+        }
+        orc_block_orth(L, L->wm, m, L->U, c, S, b);
+        for (int64_t l = 0; l < b; l++)
+            for (int64_t i = 0; i < b; i++) TB_(L, c + i, c + l) = S[i + l * b];
+        L->info->n_steps += b;
+        c += b;
+    }
+}
+
+/*
+ * Block form of Alg. 2 (k largest triplets, full re-orthogonalization).
+ *   b >= 1 block size; t = k + p (p < 0: max(15, 3k) - k); subspace sizes
+ *   t0 = b ceil(t / b) (first pass) and t1 = k + b ceil((t - k) / b) (after
+ *   each restart); needs 1 <= k, k + b <= t1, max(t0, t1) <= m and
+ *   max(t0, t1) + b <= n.
+ *   V0: n x b start block (column-major) or NULL for draws 0..b-1.
+ *   Outputs as orc_svds; Ubasis (m x tmax), Vbasis (n x (tmax + b)) and
+ *   Tout ((tmax + b) x (tmax + b)) hold the final basis and projected
+ *   matrix (tmax = max(t0, t1)); *t_last receives the size of the last
+ *   projected matrix.
+ * Returns 0 on success, -1 on bad arguments, -4 if memory ran out.
+ */
+int orc_svds_block(const orc_mat *A, int64_t k, int64_t p, int64_t b, double tol, int64_t maxit,
+                   uint64_t seed, const double *V0, double *S, double *Uout, int64_t ldu,
+                   double *Vout, int64_t ldv, double *res, orc_info *info, double *Ubasis,
+                   double *Vbasis, double *Tout, int64_t *t_last)
+{
+    memset(info, 0, sizeof(*info));
+    const int64_t m = A->m, n = A->n;
+    const int64_t t = (p < 0) ? (3 * k > 15 ? 3 * k : 15) : k + p;
+    if (b < 1 || k < 1 || t < k || !(tol > 0.0) || maxit < 1) return -1;
+    const int64_t t0 = b * ((t + b - 1) / b);
+    const int64_t t1 = k + b * ((t - k + b - 1) / b);
+    const int64_t tmax = t0 > t1 ? t0 : t1;
+    if (k + b > t1 || tmax > m || tmax + b > n) return -1;
+
+    orc_block L;
+    memset(&L, 0, sizeof(L));
+    L.A = A; L.m = m; L.n = n; L.b = b; L.ld_t = tmax + b; L.seed = seed; L.info = info;
+    L.U = (double *)calloc((size_t)(m * tmax), sizeof(double));
+    L.V = (double *)calloc((size_t)(n * (tmax + b)), sizeof(double));
+    L.T = (double *)calloc((size_t)(L.ld_t * L.ld_t), sizeof(double));
+    L.h = (double *)calloc((size_t)(L.ld_t + b * b + 2), sizeof(double));
+    L.wm = (double *)calloc((size_t)(m * b), sizeof(double));
+    L.wn = (double *)calloc((size_t)(n * b), sizeof(double));
+    double *Uh = (double *)calloc((size_t)(tmax * tmax), sizeof(double));
+    double *Vh = (double *)calloc((size_t)(tmax * tmax), sizeof(double));
+    double *Sh = (double *)calloc((size_t)tmax, sizeof(double));
+    double *Tt = (double *)calloc((size_t)(tmax * tmax), sizeof(double));
+    double *Uk = (double *)calloc((size_t)(m * k), sizeof(double));
+    double *Vk = (double *)calloc((size_t)(n * k), sizeof(double));
+    double *rho = (double *)calloc((size_t)(k * b), sizeof(double));
+    double *F = (double *)calloc((size_t)(b * b), sizeof(double));
+    if (!L.U || !L.V || !L.T || !L.h || !L.wm || !L.wn || !Uh || !Vh || !Sh || !Tt || !Uk || !Vk ||
+        !rho || !F) {
+        free(L.U); free(L.V); free(L.T); free(L.h); free(L.wm); free(L.wn);
+        free(Uh); free(Vh); free(Sh); free(Tt); free(Uk); free(Vk); free(rho); free(F);
+        return -4;
+    }
+
+    /* start block: V0 or draws 0..b-1, orthonormalized (no T entries) */
+    for (int64_t l = 0; l < b; l++) {
+        if (V0) memcpy(L.wn + l * n, V0 + l * n, sizeof(double) * (size_t)n);
+        else orc_rng_vector(seed, (uint64_t)l, n, L.wn + l * n);
+    }
+    L.draws = (uint64_t)b;
+    {
+        double *Rs = L.h + L.ld_t;
+        const double keep = L.anorm;
+        L.anorm = 0.0;  /* any nonzero column counts as independent here */
+        orc_block_orth(&L, L.wn, n, L.V, 0, Rs, b);
+        L.anorm = keep;
+        info->breakdowns = 0;
+        info->n_reorth = 0;
+    }
+    /* U(:, 0:b) R = A V(:, 0:b) */
+    for (int64_t l = 0; l < b; l++) {
+        orc_matvec(A, L.V + l * n, L.wm + l * m);
+        info->n_matvec++;
+    }
+    {
+        double *R = L.h + L.ld_t;
+        orc_block_orth(&L, L.wm, m, L.U, 0, R, b);
+        for (int64_t l = 0; l < b; l++)
+            for (int64_t i = 0; i < b; i++) TB_(&L, i, l) = R[i + l * b];
+        info->n_steps += b;
+    }
+    orc_block_lbp_from(&L, b, t0);
+
+    int64_t tc = t0;
+    for (int64_t it = 1; it <= maxit; it++) {
+        /* SVD of T(0:tc, 0:tc) */
+        for (int64_t c = 0; c < tc; c++)
+            for (int64_t r = 0; r < tc; r++) Tt[r + c * tc] = TB_(&L, r, c);
+        int sw = orc_jacobi_svd(tc, tc, Tt, tc, Sh, Uh, tc, Vh, tc, 200);
+        if (sw > info->svd_sweeps_max) info->svd_sweeps_max = sw;
+        const double smax = Sh[0];
+        if (smax > L.anorm) L.anorm = smax;
+        /* F = T(tc-b:tc, tc:tc+b); res_j = || F^T Uh(tc-b:tc, j) || / sigma_j */
+        for (int64_t l = 0; l < b; l++)
+            for (int64_t i = 0; i < b; i++) F[i + l * b] = TB_(&L, tc - b + i, tc + l);
+        int64_t nconv = 0;
+        double fnorm = 0.0;
+        for (int64_t j = 0; j < k; j++) {
+            double r2 = 0.0;
+            for (int64_t l = 0; l < b; l++) {
+                double s = 0.0;  /* (F^T u)_l = sum_i F(i, l) u_i */
+                for (int64_t i = 0; i < b; i++) s += F[i + l * b] * Uh[(tc - b + i) + j * tc];
+                rho[j + l * k] = s;  /* rho = Uh(tc-b:tc, 0:k)^T F */
+                r2 += s * s;
+            }
+            double den = Sh[j] > DBL_EPSILON * smax ? Sh[j] : DBL_EPSILON * smax;
+            double rj = (den > 0.0) ? sqrt(r2) / den : 0.0;
+            res[j] = rj;
+            if (rj < tol) nconv++;
+        }
+        for (int64_t l = 0; l < b; l++)
+            for (int64_t i = 0; i < b; i++) fnorm += F[i + l * b] * F[i + l * b];
+        info->beta_t = sqrt(fnorm);
+        info->nconv = (int32_t)nconv;
+        info->converged = (nconv == k);
+        if (info->converged || it == maxit) break;
+
+        /* augmented restart */
+        orc_gemm_nn(m, tc, k, L.U, m, Uh, tc, Uk, m);   /* U~_k = U(:, 0:tc) Uh(:, 0:k) */
+        orc_gemm_nn(n, tc, k, L.V, n, Vh, tc, Vk, n);   /* V~_k = V(:, 0:tc) Vh(:, 0:k) */
+        memset(L.T, 0, sizeof(double) * (size_t)(L.ld_t * L.ld_t));
+        for (int64_t j = 0; j < k; j++) {
+            TB_(&L, j, j) = Sh[j];
+            for (int64_t l = 0; l < b; l++) TB_(&L, j, k + l) = rho[j + l * k];
+        }
+        /* V(:, k:k+b) = V(:, tc:tc+b) */
+        memmove(L.V + k * n, L.V + tc * n, sizeof(double) * (size_t)(n * b));
+        memcpy(L.V, Vk, sizeof(double) * (size_t)(n * k));
+        memcpy(L.U, Uk, sizeof(double) * (size_t)(m * k));
+        /* W = A V(:, k:k+b) - U~_k rho, orthonormalized against U~_k */
+        for (int64_t l = 0; l < b; l++) {
+            orc_matvec(A, L.V + (k + l) * n, L.wm + l * m);
+            info->n_matvec++;
+            orc_gemv_n_sub(m, k, L.U, m, rho + l * k, L.wm + l * m);
+        }
+        {
+            double *R = L.h + L.ld_t;
+            orc_block_orth(&L, L.wm, m, L.U, k, R, b);
+            for (int64_t l = 0; l < b; l++)
+                for (int64_t i = 0; i < b; i++) TB_(&L, k + i, k + l) = R[i + l * b];
+            info->n_steps += b;
+        }
+        info->restarts++;
+        tc = t1;
+        orc_block_lbp_from(&L, k + b, t1);
+    }
+    for (int64_t j = 0; j < k; j++) S[j] = Sh[j];
+    orc_gemm_nn(m, tc, k, L.U, m, Uh, tc, Uout, ldu);
+    orc_gemm_nn(n, tc, k, L.V, n, Vh, tc, Vout, ldv);
+    orc_sign_normalize(m, n, k, Uout, ldu, Vout, ldv);
+    info->anorm_est = L.anorm;
+    if (t_last) *t_last = tc;
+    if (Ubasis) memcpy(Ubasis, L.U, sizeof(double) * (size_t)(m * tmax));
+    if (Vbasis) memcpy(Vbasis, L.V, sizeof(double) * (size_t)(n * (tmax + b)));
+    if (Tout) memcpy(Tout, L.T, sizeof(double) * (size_t)(L.ld_t * L.ld_t));
+
+    free(L.U); free(L.V); free(L.T); free(L.h); free(L.wm); free(L.wn);
+    free(Uh); free(Vh); free(Sh); free(Tt); free(Uk); free(Vk); free(rho); free(F);
+    return 0;
+}
