@@ -30,10 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "seconds to k triplets at residual ≤tol; SpMV+reorth HBM GB/s vs ~8 TB/s"
 HBM_NOMINAL_GBS = 7900.0
-# DRAM bytes (read + write) / algorithmic bytes of the top kernels, from the
-# full-size ncu captures summarised in
-# profiles/cgs2_gemv_pair_1000000x150_and_spmv_sell_zipf.md
-# ncu DRAM bytes / algorithmic bytes per kernel (1,000,000 x 150 GEMVs, full SpMV).
+# ncu DRAM bytes (read + write) / algorithmic bytes of the top kernels, from
+# one full-size capture of each: a 150-column CGS pass on the 1,000,000-row
+# basis (GEMV-T, GEMV-N) and one SpMV of the Zipf matrix.
 # GEMV-N has two layouts: update_small_kernel on the 1,000,000-row side
 # (1,213.64 MB) and update_kernel on the 500,000-row side (1,214.24 MB at
 # 1,000,000 rows), weighted 2:1 by the rows they stream in the solve.
@@ -95,6 +94,8 @@ def arm_config(A, args, k, p, tol, prec, maxit, ws):
                  if a_bytes > 129e6 else "small working set (L2-resident)")
     cfg["maxit"] = maxit
     cfg["reorth"] = args.reorth
+    if getattr(args, "block", 1) > 1:
+        cfg["block"] = args.block
     cfg["parallelism"] = "replicas" if ws > 1 else "single-gpu"
     return cfg
 
@@ -249,6 +250,148 @@ def nominal_info(m, n, nnz, k, p, restarts, sparse=True):
     return {"bytes": by, "launches": {"gemm": 2 * restarts + 2, "svd": restarts + 1}}
 
 
+# ------------------------------------------------- per-triplet error report
+
+def _g3(xs):
+    return [float(f"{float(x):.3g}") for x in xs]
+
+
+def _triplet_errors(orc, a64, k, S, U, V, ref):
+    """Per-triplet errors of a GPU result against the FP64 oracle's: sigma
+    relative error, sign-free sin(angle) of u_j and v_j, the relative gap of
+    sigma_j to its neighbours (the Wedin bound of the angle scales with
+    1 / gap), and the residuals ||A v_j - sigma_j u_j|| / sigma_1,
+    ||A^T u_j - sigma_j v_j|| / sigma_1 by the oracle's products."""
+    s = ref["S"]
+    c_u = np.sum(U * ref["U"], axis=0)
+    c_v = np.sum(V * ref["V"], axis=0)
+    gaps = np.minimum(np.r_[np.inf, s[:-1] - s[1:]], np.r_[s[:-1] - s[1:], np.inf])
+    r1 = [np.linalg.norm(orc.matvec(a64, V[:, j]) - S[j] * U[:, j]) / s[0] for j in range(k)]
+    r2 = [np.linalg.norm(orc.matvec_t(a64, U[:, j]) - S[j] * V[:, j]) / s[0] for j in range(k)]
+    rel = np.abs(S - s) / s
+    sin_u = np.linalg.norm(ref["U"] - U * c_u, axis=0)
+    sin_v = np.linalg.norm(ref["V"] - V * c_v, axis=0)
+    return {"sigma_rel_err": _g3(rel), "sin_u": _g3(sin_u), "sin_v": _g3(sin_v),
+            "gap_rel": _g3(np.where(np.isfinite(gaps), gaps / s[0], -1.0)),
+            "res_av": _g3(r1), "res_atu": _g3(r2),
+            "max": {"sigma_rel_err": float(rel.max()), "sin_u": float(sin_u.max()),
+                    "sin_v": float(sin_v.max()), "res": float(max(max(r1), max(r2)))}}
+
+
+def per_triplet_mixed(pkg, torch):
+    """Mixed form on the 2,000 x 1,000 matrix with FP32-exact values, k = p = 100:
+    every triplet against the FP64 oracle on the same matrix and start vector,
+    plus the mixed and FP64 GPU solve times on it."""
+    import oracle
+    import synth
+    oracle.build()
+    a = synth.workload_sparse_small_fp32()
+    v0 = synth.start_vector(a.n, 4)
+    k = p = 100
+    ref = oracle.svds(a, k, p, 1e-10, 100, v0=v0)
+    a32 = synth.CSR(a.m, a.n, a.row_ptr, a.col_idx, a.values.astype(np.float32))
+    times = {}
+    res = None
+    for prec, A in (("mixed", a32), ("fp64", a)):
+        with pkg.Solver(A, precision=prec) as s:
+            r = s.solve(k, p, 1e-10, 100, v0=v0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                r = s.solve(k, p, 1e-10, 100, v0=v0)
+            torch.cuda.synchronize()
+            times[prec] = (time.perf_counter() - t0) / 3
+            if prec == "mixed":
+                res = r
+    out = {"workload": "sparse 2000x1000, 1% density, values rounded to FP32, k = p = 100, tol 1e-10",
+           "vs": "FP64 oracle (oracle.svds) on the same matrix and start vector",
+           "restarts": res.info["restarts"], "oracle_restarts": ref["info"]["restarts"],
+           "mixed_gpu_s": times["mixed"], "fp64_gpu_s": times["fp64"],
+           "speedup_vs_fp64_gpu": times["fp64"] / times["mixed"]}
+    out.update(_triplet_errors(oracle, a, k, res.S, res.U, res.V, ref))
+    return out
+
+
+def batch_sample_indices(count=256, quantiles=(0.0, 0.25, 0.5)):
+    """Items of the batch at the given quantiles of their size (rows + columns)."""
+    import synth
+    sh = synth.workload_batch_shapes(count=count)
+    order = sorted(range(count), key=lambda i: sh[i][0] + sh[i][1])
+    return [order[int(q * (count - 1))] for q in quantiles]
+
+
+def per_triplet_batch(pkg, items, idx, outS, outU, outV, maxit=1000):
+    """Batched-form results of the sampled items against the FP64 oracle."""
+    import oracle
+    import synth
+    oracle.build()
+    rows = []
+    for j, i in enumerate(idx):
+        it = items[j]
+        a64 = synth.CSR(it.a.m, it.a.n, it.a.row_ptr, it.a.col_idx, it.a.values.astype(np.float64))
+        ref = oracle.svds(a64, it.k, it.k, 1e-10, maxit, seed=1)
+        d = {"index": int(i), "m": int(it.a.m), "n": int(it.a.n), "nnz": int(it.a.nnz), "k": int(it.k),
+             "oracle_restarts": ref["info"]["restarts"]}
+        d.update(_triplet_errors(oracle, a64, it.k, outS[j], outU[j], outV[j], ref))
+        rows.append(d)
+    return rows
+
+
+def per_triplet_batch_minibatch(pkg):
+    """The sampled items of the 256-matrix batch solved together in one batched
+    launch (a mini-batch; each matrix is solved by one cluster as in the full
+    batch), against the FP64 oracle."""
+    import synth
+    idx = batch_sample_indices()
+    items = synth.workload_batch(only=idx)
+    b = pkg.Batch([it.a for it in items], [it.k for it in items], seed=1)
+    out = b.solve(1e-10, 1000)
+    lay = b.layout()
+    b.close()
+    return {"vs": "FP64 oracle (oracle.svds) on the FP64 copy of each matrix",
+            "solved_as": f"mini-batch of the {len(idx)} sampled items, {lay['cluster_size']} CTAs per matrix",
+            "items": per_triplet_batch(pkg, items, idx, out["S"], out["U"], out["V"])}
+
+
+# ------------------------------------------------------ block form compare
+
+def block_comparison(pkg, torch, A, k, p, tol, maxit, S_ref, blocks=(1, 4, 8, 16), precs=("mixed",)):
+    """The block form (b Lanczos vectors per step) against the single-vector
+    form (b = 1) on the same workload: one untimed and one timed solve each
+    (CUDA events), restarts, products, and the algorithmic bytes of the
+    products and CGS passes over the solve time; sigma against S_ref (the
+    FP64 single-vector solve of the bench)."""
+    import synth
+    out = []
+    for prec in precs:
+        A_p = A
+        if prec == "mixed" and hasattr(A, "row_ptr") and A.values.dtype != np.float32:
+            A_p = synth.CSR(A.m, A.n, A.row_ptr, A.col_idx, A.values.astype(np.float32))
+        for b in blocks:
+            row = {"precision": prec, "block": b}
+            try:
+                with pkg.Solver(A_p, precision=prec, block=b) as s:
+                    r = s.solve(k, p, tol, maxit)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    r = s.solve(k, p, tol, maxit)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    sec = e0.elapsed_time(e1) / 1e3
+                inf = r.info
+                by = sum(inf["bytes"][ph] for ph in ("spmv", "gemv_t", "gemv_n"))
+                S = np.asarray(r.S)
+                row.update({"seconds": sec, "restarts": inf["restarts"], "converged": inf["converged"],
+                            "n_matvec": inf["n_matvec"], "t_last": inf["t"], "launches": inf["n_launches"],
+                            "spmv_reorth_bytes": by, "alg_gbs_over_solve": by / sec / 1e9,
+                            "sigma_rel_err_vs_fp64_single_max": float(np.max(np.abs(S - S_ref) / S_ref))})
+            except Exception as exc:  # a size the block form rejects
+                row["error"] = str(exc)
+            out.append(row)
+    return out
+
+
 # -------------------------------------------------------------------- main
 
 def dist_setup(args):
@@ -370,6 +513,9 @@ def run_batch(args, ws, rank):
     rs = np.array([i["restarts"] for i in infos])
     balance = {"cluster_busy_s_max": float(loads.max()), "cluster_busy_s_mean": float(loads.mean()),
                "svd_share": float(prof["cycles_svd"].sum() / max(1, prof["cycles_total"].sum())),
+               "phase_share": {nm: float(prof["cycles_phase"][:, q].sum() / max(1, prof["cycles_total"].sum()))
+                               for q, nm in enumerate(("spmv", "cgs_fp32", "cgs_fp64", "norm_scale",
+                                                       "restart_gemm"))},
                "lbp_share": float(prof["cycles_lbp"].sum() / max(1, prof["cycles_total"].sum())),
                "restarts_max": int(rs.max()), "restarts_p90": float(np.percentile(rs, 90)),
                "slowest_matrix_s": float(prof["cycles_total"].max() / clk),
@@ -396,6 +542,16 @@ def run_batch(args, ws, rank):
         Sb = out["S"][i].cpu().numpy()
         errs.append(float(np.max(np.abs(Sb - r.S) / r.S)))
     plain_est = plain_s / len(sample) * count
+    per_triplet = None
+    if not args.no_per_triplet:
+        idx = batch_sample_indices(count) if (count == 256 and args.scale == 1.0) else [0]
+        tonp = lambda x: x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+        per_triplet = {"vs": "FP64 oracle (oracle.svds) on the FP64 copy of each matrix",
+                       "solved_as": "items of the timed batch solve",
+                       "items": per_triplet_batch(pkg, [items[i] for i in idx], idx,
+                                                  [tonp(out["S"][i]) for i in idx],
+                                                  [tonp(out["U"][i]) for i in idx],
+                                                  [tonp(out["V"][i]) for i in idx])}
     peaks, src = load_peaks()
     gbs = tot_bytes / wall / 1e9
     res = {"metric": METRIC, "value": wall, "unit": "s", "n_gpus": ws, "steps": args.steps,
@@ -411,7 +567,8 @@ def run_batch(args, ws, rank):
                      "sigma_rel_err_vs_plain_fp64_max": max(errs), "plain_sample": len(sample),
                      "balance": balance},
            "hbm": {"alg_gbs": gbs, "frac_of_measured": gbs / peaks["hbm_gbs"]},
-           "gpu_launches": launches, "clocks": clocks, "cpu_baseline": None, "e2e": None}
+           "gpu_launches": launches, "clocks": clocks, "cpu_baseline": None, "e2e": None,
+           "per_triplet": per_triplet}
     print(json.dumps(res), flush=True)
     b.close()
     return 0
@@ -484,6 +641,14 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="shrinks the large workloads (testing only)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block-compare", type=int, nargs="*", default=[1, 4, 8, 16],
+                    help="block sizes of the block-form comparison on the workload (mixed precision); "
+                         "empty to skip")
+    ap.add_argument("--block-fp64", action="store_true", help="also compare the FP64 block form")
+    ap.add_argument("--block", type=int, default=1, help="block size of the timed solves (1: single vector)")
+    ap.add_argument("--no-per-triplet", action="store_true",
+                    help="skip the per-triplet error report (mixed form on the 2,000 x 1,000 matrix and "
+                         "a batch sample, against the FP64 oracle)")
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--ref-restarts", type=int, default=None)
     ap.add_argument("--reorth", choices=["full", "partial"], default="full",
@@ -546,8 +711,9 @@ def main():
     stream = torch.cuda.current_stream()
     # the headline is timed without per-launch events; a second, instrumented
     # context (timing=True) times every launch for the phase and roofline figures
-    solver = pkg.Solver(A, precision=prec, timing=False, stream=stream.cuda_stream, reorth=args.reorth)
-    v0_dev = torch.tensor(v0, device="cuda")
+    solver = pkg.Solver(A, precision=prec, timing=False, stream=stream.cuda_stream, reorth=args.reorth,
+                        block=args.block)
+    v0_dev = torch.tensor(v0, device="cuda") if args.block <= 1 else None  # block form: seeded start block
     outs = (torch.empty(k, dtype=torch.float64, device="cuda"),
             torch.empty((k, A.m), dtype=torch.float64, device="cuda"),
             torch.empty((k, A.n), dtype=torch.float64, device="cuda"),
@@ -576,7 +742,8 @@ def main():
     ms = allreduce_max(ms, ws)
 
     # instrumented pass: the same solves with CUDA events around every launch
-    solver_t = pkg.Solver(A, precision=prec, timing=True, stream=stream.cuda_stream, reorth=args.reorth)
+    solver_t = pkg.Solver(A, precision=prec, timing=True, stream=stream.cuda_stream, reorth=args.reorth,
+                          block=args.block)
     solver_t.solve(k, p, tol, maxit, v0=v0_dev, outputs=outs)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -646,10 +813,10 @@ def main():
         for it in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with pkg.Solver(hp, precision=prec, reorth=args.reorth) as s2:
+            with pkg.Solver(hp, precision=prec, reorth=args.reorth, block=args.block) as s2:
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
-                r2 = s2.solve(k, p, tol, maxit, v0=hv0, outputs=hout)
+                r2 = s2.solve(k, p, tol, maxit, v0=hv0 if args.block <= 1 else None, outputs=hout)
                 t2 = time.perf_counter()
             torch.cuda.synchronize()
             if it > 0:
@@ -676,10 +843,25 @@ def main():
 
     mixed_vs_fp64 = None
     if ref_fp64 is not None:
+        # the oracle cannot solve this workload in bench time; the mixed solve is
+        # compared with the GPU's FP64 solve of the same rounded matrix here, and
+        # per triplet with the oracle on the 2,000 x 1,000 workload (per_triplet)
         Sm = r.S.cpu().numpy() if hasattr(r.S, "cpu") else np.asarray(r.S)
         mixed_vs_fp64 = {"fp64_gpu_s": ref_fp64_s, "speedup": ref_fp64_s / (ms / 1e3),
-                         "sigma_rel_err_max": float(np.max(np.abs(Sm - ref_fp64.S) / ref_fp64.S)),
+                         "sigma_rel_err_max_vs_fp64_gpu": float(np.max(np.abs(Sm - ref_fp64.S) / ref_fp64.S)),
                          "fp64_restarts": ref_fp64.info["restarts"]}
+    block_form = None
+    if rank == 0 and ws == 1 and args.block_compare and hasattr(A, "row_ptr") and args.reorth == "full":
+        S_ref = r.S.cpu().numpy() if hasattr(r.S, "cpu") else np.asarray(r.S)
+        block_form = {"workload": cfg["workload"], "k": k, "p": p, "tol": tol,
+                      "note": "b = 1 is the single-vector method; t0 = b ceil((k+p)/b), t1 = k + b ceil(p/b)",
+                      "runs": block_comparison(pkg, torch, A, k, p, tol, maxit, S_ref,
+                                               blocks=tuple(args.block_compare),
+                                               precs=("mixed", "fp64") if args.block_fp64 else ("mixed",))}
+    per_triplet = None
+    if rank == 0 and ws == 1 and not args.no_per_triplet:
+        per_triplet = {"mixed_2000x1000_k100": per_triplet_mixed(pkg, torch),
+                       "batch_sample": per_triplet_batch_minibatch(pkg)}
     vs_base, paper = None, None
     if args.workload in PAPER_S and args.scale == 1.0:
         # same size, spectrum, k, t, tol and round cap as the paper's DenseN; its
@@ -697,7 +879,8 @@ def main():
                      "n_matvec": info["n_matvec"], "breakdowns": info["breakdowns"], "t": info["t"],
                      "phase_ms_per_step": phases_ms, "anorm_est": info["anorm_est"],
                      "sigma_1": float(r.S[0]), "sigma_k": float(r.S[k - 1])},
-           "mixed_vs_fp64": mixed_vs_fp64, "paper": paper}
+           "mixed_vs_fp64": mixed_vs_fp64, "per_triplet": per_triplet, "block_form": block_form,
+           "paper": paper}
     if rank == 0:
         print(json.dumps(out), flush=True)
     solver.close()

@@ -104,6 +104,19 @@ typedef struct svdsc_matrix {
  * kind) to the same CGS2 only when an estimate exceeds eps^(3/4); the basis
  * is then orthogonal to ~eps^(3/4) (|u_i^T u_j| <~ 1e-11) instead of ~eps.
  * Fewer bytes, less robust; the batched form supports SVDSC_REORTH_FULL only.
+ * block: 0 or 1 runs the single-vector method above; 2, 4, 8 or 16 runs its
+ * block form (block Lanczos bidiagonalization of Golub, Luk & Overton 1981,
+ * carried through the full re-orthogonalization of Sec. 2.1 and the
+ * augmented restart of Alg. 2): each step forms b Lanczos vectors with one
+ * sparse product A X (X n x b), re-orthogonalizes them together (two block
+ * classical Gram-Schmidt passes) and orthonormalizes them within the block
+ * (two Cholesky QR passes; a block that is numerically rank-deficient or
+ * ill-conditioned is redone column by column).  The projected matrix is upper
+ * triangular with bandwidth b; the residual of Eq. (4) becomes
+ * ||F^T Uh(t-b:t, j)|| / sigma_j with F the b x b block that couples the last
+ * block to the residual block.  The subspace is t0 = b ceil((k+p)/b) columns
+ * in the first pass and t1 = k + b ceil(p/b) after each restart.  CSR input,
+ * SVDSC_LARGEST and SVDSC_REORTH_FULL only; FP64 or mixed precision.
  */
 typedef struct svdsc_options {
     int32_t precision;
@@ -113,6 +126,7 @@ typedef struct svdsc_options {
     int32_t batch_cluster; /* batched form: CTAs (one cluster) per matrix, 1, 2, 4 or 8; 0 = automatic */
     int32_t which;         /* SVDSC_LARGEST (default) or SVDSC_SMALLEST */
     int32_t reorth;        /* SVDSC_REORTH_FULL (default) or SVDSC_REORTH_PARTIAL */
+    int32_t block;         /* Lanczos block size: 0 or 1 (single vector, default), 2, 4, 8 or 16 */
 } svdsc_options;
 
 /* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
@@ -175,7 +189,11 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
  *   maxit >= 1: number of projected-SVD-and-test rounds; the last round never
  *   restarts (at most maxit - 1 restarts).
  *   v0: start vector (n entries, host or device per v0_on_device) or NULL for
- *   the seeded random draw.
+ *   the seeded random draw; in the block form (options.block = b > 1) a
+ *   start block of n x b entries (column-major, ld n), or NULL for draws
+ *   0..b-1.  Block form sizes: t0 = b ceil(t/b), t1 = k + b ceil((t-k)/b),
+ *   needs k + b <= t1, max(t0, t1) <= m, max(t0, t1) + b <= n and
+ *   max(t0, t1) <= 448.
  *   Outputs (written on success or SVDSC_NOT_CONVERGED): S[k] descending
  *   (ascending for SVDSC_SMALLEST: the smallest first),
  *   U (m x k, column-major, ldu >= m), V (n x k, ldv >= n), res[k] (may be
@@ -252,11 +270,14 @@ int svdsc_reserve(svdsc_ctx *ctx, int t);
  * Restart / output basis update of Alg. 2 on the tensor cores:
  * C = W Q with W rows x t (leading dimension ldw), Q t x k (ldq), C rows x k
  * (ldc), all column-major FP64 device arrays; C must not overlap W.
- *   mode 0 (FP64 form): both operands are cut into nine signed 6-bit digit
- *   slices on power-of-two row / column scales (an Ozaki-style error-free
- *   split), the 45 slice products run as BF16 tcgen05 MMAs whose FP32
- *   accumulations are exact integers, and the epilogue recombines them
- *   exactly before one FP64 rounding: accuracy of an FP64 GEMM (needs
+ *   mode 0 (FP64 form): on power-of-two row (W) and column (Q) scales every
+ *   entry becomes a fixed-point integer below 2^54, cut into eight balanced
+ *   base-128 digits in [-64, 63] (an Ozaki-style error-free split); the 36
+ *   digit products of weight s + s' <= 7 run as BF16 tcgen05 MMAs into eight
+ *   TMEM accumulators, one per weight, whose FP32 sums are exact integers;
+ *   the epilogue recombines them exactly in integer arithmetic before one
+ *   FP64 rounding.  The dropped products (weight >= 8) and the 2^-54
+ *   truncation keep the error inside the bound of an FP64 GEMM (needs
  *   t <= 448).
  *   mode 1 (mixed form): W rounded to FP32 and Q are cut into three BF16 pieces
  *   each; the six leading piece products accumulate in FP32 (about FP32
@@ -277,14 +298,18 @@ int svdsc_gemm(svdsc_ctx *ctx, int mode, int64_t rows, int t, int k, const doubl
  * hosts that only hand a library pre-allocated buffers.  The paper has no
  * counterpart; it exists only for such callers.
  *   Scratch: one file-scope __device__ array of 4.3 MB (532,992 doubles) that
- *   every GPU loading this library holds until the process exits.  Limits:
- *   ncols <= 512 and len <= 4,194,304 (at most 1,024 row chunks of 4,096);
- *   larger sizes return SVDSC_ERR_SIZE before any GPU work.
- *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.  Every call shares the array and overwrites
- *   what it reads, so calls whose GPU work overlaps (two streams, two host
- *   threads) race and give wrong results; serialize them.
+ *   every CUDA context loading this library holds until the process exits.
+ *   Limits: ncols <= 512 and len <= 4,194,304 (at most 1,024 row chunks of
+ *   4,096); larger sizes return SVDSC_ERR_SIZE before any GPU work.
+ *   The first call in a CUDA context looks up the array's device address
+ *   (cudaGetSymbolAddress, with that context current) and remembers it under
+ *   the context's unique ID; a new context (for example after
+ *   cudaDeviceReset) gets its own lookup on its first call.  Make that first
+ *   call outside any stream capture: while `stream` is being captured, a
+ *   context that has not called before gets SVDSC_ERR_ARG.  Every call shares
+ *   the array and overwrites what it reads, so calls whose GPU work overlaps
+ *   (two streams, two host threads) race and give wrong results; serialize
+ *   them.
  *   W (len x ncols, leading dimension ldw, even, 16-byte aligned), w (len,
  *   16-byte aligned, overwritten), norm_out (one double): device pointers.
  *   stream: cudaStream_t or NULL.  The call only enqueues the work on stream
@@ -341,6 +366,13 @@ int svdsc_batch_layout(const svdsc_batch *b, int *cluster_size, int *clusters);
  * solved the matrix. */
 int svdsc_batch_profile(const svdsc_batch *b, int64_t *cycles_total, int64_t *cycles_svd,
                         int64_t *cycles_lbp, int32_t *cluster);
+
+/* Per-matrix SM clock cycles of the last batch solve by phase, on the
+ * cluster's first CTA (nb x 5 entries, row-major): [0] sparse products,
+ * [1] the FP32 CGS pass, [2] the FP64 CGS pass with the norm, [3] the
+ * normalization / breakdown test / scaling, [4] the restart and output
+ * GEMMs with the sign rule.  Each phase includes its cluster barriers. */
+int svdsc_batch_phase_cycles(const svdsc_batch *b, int64_t *cycles);
 
 int svdsc_batch_destroy(svdsc_batch *b);
 

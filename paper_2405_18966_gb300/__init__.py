@@ -34,6 +34,7 @@ EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "sv
            "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc",
            "svdsc_gemm", "svdsc_batch_create", "svdsc_batch_solve", "svdsc_batch_tuning",
            "svdsc_batch_destroy", "svdsc_solve_batched", "svdsc_batch_layout", "svdsc_batch_profile",
+           "svdsc_batch_phase_cycles",
            "svdsc_selftest_wait")
 
 
@@ -48,7 +49,7 @@ class SvdscMatrix(C.Structure):
 class SvdscOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("timing", C.c_int32), ("seed", C.c_uint64),
                 ("restart_gemm", C.c_int32), ("batch_cluster", C.c_int32), ("which", C.c_int32),
-                ("reorth", C.c_int32)]
+                ("reorth", C.c_int32), ("block", C.c_int32)]
 
 
 NUM_PHASES = 8
@@ -104,6 +105,7 @@ def lib():
         L.svdsc_batch_destroy.argtypes = [vp]
         L.svdsc_batch_layout.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.svdsc_batch_profile.argtypes = [vp, vp, vp, vp, vp]
+        L.svdsc_batch_phase_cycles.argtypes = [vp, vp]
         L.svdsc_selftest_wait.argtypes = [vp, i32]
         L.svdsc_solve_batched.argtypes = [i32, C.POINTER(SvdscMatrix), vp, vp, dbl, i32, vp, vp, vp, vp,
                                           i32, C.POINTER(SvdscOptions), C.POINTER(SvdscInfo)]
@@ -153,7 +155,8 @@ class Solver:
     """A matrix prepared on the device (svdsc_create) that can be solved many times."""
 
     def __init__(self, A, precision: str = "fp64", seed: int = 0, stream=None, timing: bool = False,
-                 restart_gemm: str = "tensor", which: str = "largest", reorth: str = "full"):
+                 restart_gemm: str = "tensor", which: str = "largest", reorth: str = "full",
+                 block: int = 1):
         self._keep = []
         self.handle = C.c_void_p()
         prec = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -191,7 +194,9 @@ class Solver:
             mat.value_type = F64
             self.m, self.n = int(a.shape[0]), int(a.shape[1])
         opt = SvdscOptions(prec, int(timing), seed, {"tensor": 0, "fma": 1}[restart_gemm], 0,
-                           {"largest": 0, "smallest": 1}[which], {"full": 0, "partial": 1}[reorth])
+                           {"largest": 0, "smallest": 1}[which], {"full": 0, "partial": 1}[reorth],
+                           int(block))
+        self.block = int(block)
         st = None if stream is None else C.c_void_p(int(stream))
         self.stream = stream
         _check(lib().svdsc_create(C.byref(self.handle), C.byref(mat), C.byref(opt), st), "svdsc_create")
@@ -239,10 +244,13 @@ class Solver:
             on_dev = True
         v0p, v0dev = None, 0
         if v0 is not None:
+            # block form: an n x b start block, passed column-major
             if _is_torch(v0):
+                if v0.dim() == 2:
+                    v0 = v0.t().contiguous()
                 v0p, v0dev = _ptr(v0), int(v0.is_cuda)
             else:
-                v0 = np.ascontiguousarray(v0, dtype=np.float64)
+                v0 = np.asfortranarray(v0, dtype=np.float64)
                 v0p = _ptr(v0)
         status = _check(lib().svdsc_solve(self.handle, k, p, tol, maxit, v0p, v0dev, _ptr(S), _ptr(U),
                                           self.m, _ptr(V), self.n, _ptr(res), int(on_dev),
@@ -327,7 +335,7 @@ class Batch:
         self.k = np.ascontiguousarray(k, dtype=np.int32)
         self.p = np.ascontiguousarray(p if p is not None else self.k, dtype=np.int32)
         self.shapes = [(int(a.m), int(a.n)) for a in mats]
-        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0, 0)
+        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0, 0, 0)
         self.handle = C.c_void_p()
         _check(lib().svdsc_batch_create(C.byref(self.handle), nb, arr, _ptr(self.k), _ptr(self.p),
                                         C.byref(opt), None), "svdsc_batch_create")
@@ -343,7 +351,10 @@ class Batch:
         cl = np.zeros(nb, dtype=np.int32)
         _check(lib().svdsc_batch_profile(self.handle, _ptr(tot), _ptr(svd), _ptr(lbp), _ptr(cl)),
                "svdsc_batch_profile")
-        return {"cycles_total": tot, "cycles_svd": svd, "cycles_lbp": lbp, "cluster": cl}
+        ph = np.zeros((nb, 5), dtype=np.int64)
+        _check(lib().svdsc_batch_phase_cycles(self.handle, _ptr(ph)), "svdsc_batch_phase_cycles")
+        return {"cycles_total": tot, "cycles_svd": svd, "cycles_lbp": lbp, "cluster": cl,
+                "cycles_phase": ph}
 
     def tuning(self, i):
         a, b, c, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
@@ -394,8 +405,9 @@ class Batch:
 
 def svds(A, k: int, p: int = -1, tol: float = 1e-10, maxit: int = 100, precision: str = "fp64",
          seed: int = 0, v0=None, out: str = "host", restart_gemm: str = "tensor",
-         which: str = "largest", reorth: str = "full") -> Result:
-    """One-shot convenience: create, solve, destroy."""
+         which: str = "largest", reorth: str = "full", block: int = 1) -> Result:
+    """One-shot convenience: create, solve, destroy.  block = b > 1 runs the
+    block form (v0, if given, is an n x b start block)."""
     with Solver(A, precision=precision, seed=seed, restart_gemm=restart_gemm, which=which,
-                reorth=reorth) as s:
+                reorth=reorth, block=block) as s:
         return s.solve(k, p, tol, maxit, v0=v0, out=out)

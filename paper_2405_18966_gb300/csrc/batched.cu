@@ -53,6 +53,7 @@ struct BStat {
     int err, svd_sweeps;
     int64_t cycles_total, cycles_svd, cycles_lbp;  // SM clock cycles on the cluster leader
     int cluster, pad;
+    int64_t cycles_phase[5];  // SpMV, FP32 CGS pass, FP64 CGS pass, norm/scale, restart/output GEMM
 };
 
 struct BSlot {   // one per cluster (bases), T one per CTA
@@ -160,7 +161,7 @@ __device__ __forceinline__ double cta_sum(double v, double *red)
 
 template <int G>
 __device__ void cta_spmv_g(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                           const float *__restrict__ val, const float *__restrict__ x, int64_t rows,
+                           const float *__restrict__ val, const float *x, int64_t rows,
                            const double *__restrict__ z, double coef, double *__restrict__ y)
 {
     const int grp = threadIdx.x / G, lg = threadIdx.x % G;
@@ -169,11 +170,14 @@ __device__ void cta_spmv_g(const int64_t *__restrict__ rp, const int32_t *__rest
         const int64_t e0 = rp[r], e1 = rp[r + 1];
         float a0 = 0.f, a1 = 0.f;
         int64_t e = e0 + lg;
+        // the matrix streams with evict-first loads; x was written earlier in this
+        // launch by the cluster's CTAs, so it is read with ordinary (coherent)
+        // loads, never through the read-only path
         for (; e + G < e1; e += 2 * G) {
-            a0 = fmaf(__ldg(val + e), __ldg(x + __ldg(col + e)), a0);
-            a1 = fmaf(__ldg(val + e + G), __ldg(x + __ldg(col + e + G)), a1);
+            a0 = fmaf(__ldcs(val + e), x[__ldcs(col + e)], a0);
+            a1 = fmaf(__ldcs(val + e + G), x[__ldcs(col + e + G)], a1);
         }
-        if (e < e1) a0 = fmaf(__ldg(val + e), __ldg(x + __ldg(col + e)), a0);
+        if (e < e1) a0 = fmaf(__ldcs(val + e), x[__ldcs(col + e)], a0);
         float s = a0 + a1;
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
@@ -204,7 +208,7 @@ __device__ void cta_spmv(int G, const int64_t *rp, const int32_t *col, const flo
 constexpr int kRowParts = 8;
 
 template <typename WT, int TC>
-__device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, const WT *__restrict__ w,
+__device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, const WT *w,
                            int64_t len, double *h, double *part)
 {
     using AT = WT;  // FP32 products and sums for the FP32 shadow, FP64 otherwise
@@ -226,7 +230,7 @@ __device__ void cta_proj_t(const WT *__restrict__ W, int64_t ld, int ncols, cons
             AT wr[4];
             WT v[TC][4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) wr[u] = (AT)__ldg(w + r + 32 * u);
+            for (int u = 0; u < 4; u++) wr[u] = (AT)w[r + 32 * u];  // written in this launch: coherent loads
 #pragma unroll
             for (int q = 0; q < TC; q++)
 #pragma unroll
@@ -348,6 +352,7 @@ struct BRun {
     float *smf;
     bool failed;
     bool lead;                 // rank 0 of the cluster writes the per-matrix outputs
+    long long cyc[5];          // SM cycles per phase (see BStat::cycles_phase)
 };
 
 __device__ __forceinline__ double *Tb(BRun &R, int r, int c) { return R.T + r + (int64_t)c * (R.t + 1); }
@@ -392,6 +397,7 @@ __device__ double cl_cgs2(BRun &R, const double *W, const float *W32, int64_t ld
     float *h32 = R.smf + kSmH32;
     const int64_t len = r1 - r0;
     if (ncols <= 0) return cl_sum_scalar(R, cta_norm2(w + r0, len, red));
+    const long long c0 = clock64();
     for (int64_t j = threadIdx.x; j < len; j += kBT) R.wf[r0 + j] = (float)w[r0 + j];
     __syncthreads();
     cta_proj<float>(R.tc, W32 + r0, ld, ncols, R.wf + r0, len, part_buf(R), R.sm + kSmRowPart);
@@ -399,9 +405,13 @@ __device__ double cl_cgs2(BRun &R, const double *W, const float *W32, int64_t ld
     for (int c = threadIdx.x; c < ncols; c += kBT) h32[c] = (float)h[c];
     __syncthreads();
     cta_update<float, float>(W32 + r0, ld, ncols, h32, w + r0, len, false, red);
+    const long long c1 = clock64();
     cta_proj<double>(R.tc, W + r0, ld, ncols, w + r0, len, part_buf(R), R.sm + kSmRowPart);
     cl_gather(R, ncols, h);
-    return cl_sum_scalar(R, cta_update<double, double>(W + r0, ld, ncols, h, w + r0, len, true, red));
+    const double n2 = cl_sum_scalar(R, cta_update<double, double>(W + r0, ld, ncols, h, w + r0, len, true, red));
+    R.cyc[1] += c1 - c0;
+    R.cyc[2] += clock64() - c1;
+    return n2;
 }
 
 // Normalises the freshly orthogonalized column `col` of side (0: U, 1: V);
@@ -456,20 +466,28 @@ __device__ void lbp_from(BRun &R, int s)
     for (int i = s; i <= R.t && !R.failed; i++) {
         // v_{i+1} = A^T u_i - alpha_i v_i, CGS2 against v_1..v_i
         double *vout = R.V + (int64_t)i * R.ldv;
+        long long c0 = clock64();
         cta_spmv(M.gAT, M.rpT + R.n0, M.colT, M.valT, R.U32 + (int64_t)(i - 1) * R.ldu, R.n1 - R.n0,
                  R.V + (int64_t)(i - 1) * R.ldv + R.n0, *Tb(R, i - 1, i - 1), vout + R.n0);
+        R.cyc[0] += clock64() - c0;
         double n2 = cl_cgs2(R, R.V, R.V32, R.ldv, i, vout, R.n0, R.n1);
+        c0 = clock64();
         const double beta = finish_vector(R, 1, i, n2);
+        R.cyc[3] += clock64() - c0;
         if (threadIdx.x == 0) *Tb(R, i - 1, i) = beta;
         __syncthreads();
         if (threadIdx.x == 0 && R.lead) { R.st->n_matvec++; R.st->n_steps++; }
         if (i == R.t) break;
         // u_{i+1} = A v_{i+1} - beta_i u_i, CGS2 against u_1..u_i
         double *uout = R.U + (int64_t)i * R.ldu;
+        c0 = clock64();
         cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32 + (int64_t)i * R.ldv, R.m1 - R.m0,
                  R.U + (int64_t)(i - 1) * R.ldu + R.m0, beta, uout + R.m0);
+        R.cyc[0] += clock64() - c0;
         n2 = cl_cgs2(R, R.U, R.U32, R.ldu, i, uout, R.m0, R.m1);
+        c0 = clock64();
         const double alpha = finish_vector(R, 0, i, n2);
+        R.cyc[3] += clock64() - c0;
         if (threadIdx.x == 0) *Tb(R, i, i) = alpha;
         __syncthreads();
         if (threadIdx.x == 0 && R.lead) { R.st->n_matvec++; R.st->n_steps++; }
@@ -664,6 +682,7 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
     R.sm = sm;
     R.smf = smf;
     R.failed = false;
+    for (int q = 0; q < 5; q++) R.cyc[q] = 0;
     double *red = sm + kSmRed;
     const int t = R.t, k = R.k;
     const long long c_start = clock64();
@@ -723,8 +742,10 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
         __syncthreads();
         if (nconv == k || it == P.maxit) break;
         // augmented restart: this CTA's rows of U~ = U(:,1:t) Uh(:,1:k), V~ = V(:,1:t) Vh(:,1:k)
+        const long long cg = clock64();
         cta_gemm32(R.U32 + R.m0, R.ldu, R.m1 - R.m0, t, R.smf + kSmQU, k, R.Ua + R.m0, R.U32a + R.m0, R.ldu);
         cta_gemm32(R.V32 + R.n0, R.ldv, R.n1 - R.n0, t, R.smf + kSmQV, k, R.Va + R.n0, R.V32a + R.n0, R.ldv);
+        R.cyc[4] += clock64() - cg;
         for (int64_t j = R.n0 + threadIdx.x; j < R.n1; j += kBT) {  // v_{k+1} = v_{t+1}
             R.Va[j + (int64_t)k * R.ldv] = R.V[j + (int64_t)t * R.ldv];
             R.V32a[j + (int64_t)k * R.ldv] = R.V32[j + (int64_t)t * R.ldv];
@@ -761,17 +782,20 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
     }
     if (!R.failed) {
         // outputs: S, this CTA's rows of U = U(:,1:t) Uh(:,1:k), V = V(:,1:t) Vh(:,1:k), sign rule
+        const long long cg = clock64();
         if (R.lead)
             for (int j = threadIdx.x; j < k; j += kBT) M.S[j] = sm[kSmS + j];
         cta_gemm32(R.U32 + R.m0, R.ldu, R.m1 - R.m0, t, smf + kSmQU, k, M.U + R.m0, nullptr, R.m);
         cta_gemm32(R.V32 + R.n0, R.ldv, R.n1 - R.n0, t, smf + kSmQV, k, M.V + R.n0, nullptr, R.n);
         cl_sign(R, M.U, R.m, M.V, R.n);
+        R.cyc[4] += clock64() - cg;
         if (threadIdx.x == 0 && R.lead) st->anorm = R.anorm;
     }
     if (threadIdx.x == 0 && R.lead) {
         st->cycles_total = clock64() - c_start;
         st->cycles_svd = c_svd;
         st->cycles_lbp = c_lbp;
+        for (int q = 0; q < 5; q++) st->cycles_phase[q] = R.cyc[q];
     }
     phase = R.phase;
 }
@@ -1235,6 +1259,17 @@ int svdsc_batch_profile(const svdsc_batch *B, int64_t *cycles_total, int64_t *cy
         if (cycles_lbp) cycles_lbp[b] = st[b].cycles_lbp;
         if (cluster) cluster[b] = st[b].cluster;
     }
+    return SVDSC_OK;
+}
+
+int svdsc_batch_phase_cycles(const svdsc_batch *B, int64_t *cycles)
+{
+    if (!B || !cycles) return SVDSC_ERR_ARG;
+    std::vector<BStat> st(B->nb);
+    if (cudaMemcpy(st.data(), B->d_stats, sizeof(BStat) * B->nb, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SVDSC_ERR_CUDA;
+    for (int b = 0; b < B->nb; b++)
+        for (int q = 0; q < 5; q++) cycles[(int64_t)b * 5 + q] = st[b].cycles_phase[q];
     return SVDSC_OK;
 }
 

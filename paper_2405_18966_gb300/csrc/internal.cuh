@@ -152,6 +152,8 @@ void update_sub(const double *W, int64_t ld, int ncols, const double *h, double 
 void update_sub_f32(const float *W32, int64_t ld, int ncols, const double *h, double *w,
                     const Chunk &c, const int *poison, cudaStream_t s);
 void norm_partial(const double *w, const Chunk &c, double *Pn, const int *poison, cudaStream_t s);
+// *out = ||w||_2 from the partial sums norm_partial / the last GEMV-N pass left (nb = Chunk::nbu)
+void norm_from_partials(const double *Pn, int nb, double *out, cudaStream_t s);
 // mode: 0 = Lanczos vector (T entry := norm, breakdown check), 1 = plain normalise
 // (no T entry), 2 = repair of a breakdown (T entry := 0, needs norm > 1e-8)
 void finalize(double *w, const Chunk &c, const double *Pn, double *T_entry, DevStatus *st,

@@ -11,6 +11,8 @@
 // fixed size.  Every GPU that loads this library holds that array until the
 // process exits.  The paper has no counterpart of this entry point.
 #include <mutex>
+#include <cuda.h>  // CUcontext / CUresult types; the two driver calls come from cudaGetDriverEntryPointByVersion
+#include "ctx_cache.h"
 #include "internal.cuh"
 
 namespace svdsc {
@@ -20,44 +22,69 @@ constexpr int kNoAllocMaxChunks = 1024;    // row chunks of <= 4096 rows: len <=
 constexpr int kNoAllocMaxNormParts = 8192; // GEMV-N CTAs of >= 512 rows at that length
 constexpr size_t kNoAllocDoubles =
     (size_t)kNoAllocMaxChunks * kNoAllocMaxCols + kNoAllocMaxCols + kNoAllocMaxNormParts;
-constexpr int kNoAllocMaxDevices = 64;
 
-// 4.3 MB of scratch per device: P (ncols x chunks), h (ncols), Pn (GEMV-N CTAs).
+// 4.3 MB of scratch per context: P (ncols x chunks), h (ncols), Pn (GEMV-N CTAs).
 static __device__ __align__(256) double g_cgs2_scratch[kNoAllocDoubles];
 
-static std::mutex g_scratch_mu;
-static double *g_scratch_addr[kNoAllocMaxDevices] = {nullptr};
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the name itself is only a host-side stand-in).
-static int scratch_address(double **out)
+static std::mutex g_scratch_mu;
+static CtxAddrCache<64> g_scratch_addr;  // context ID -> device address of g_cgs2_scratch
+
+static bool driver_calls(CtxGetCurrentFn *cur, CtxGetIdFn *id)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SVDSC_ERR_CUDA;
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return SVDSC_ERR_ARG;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    static std::once_flag once;
+    static CtxGetCurrentFn f_cur = nullptr;
+    static CtxGetIdFn f_id = nullptr;
+    std::call_once(once, [] {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_cgs2_scratch) != cudaSuccess || !p) return SVDSC_ERR_CUDA;
-        g_scratch_addr[dev] = (double *)p;
-    }
-    *out = g_scratch_addr[dev];
-    return SVDSC_OK;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            f_cur = (CtxGetCurrentFn)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            f_id = (CtxGetIdFn)p;
+    });
+    *cur = f_cur;
+    *id = f_id;
+    return f_cur && f_id;
 }
 
-__global__ void noalloc_norm_kernel(const double *__restrict__ Pn, int nb, double *out)
+// Device address of the scratch array in the current context.  The array is
+// placed anew in every context that loads this module (after a device reset,
+// or in a second context on the same device), so the address is cached per
+// context ID and looked up (cudaGetSymbolAddress, with that context current)
+// the first time a context calls.  That lookup is refused while `s` is being
+// captured into a CUDA graph (SVDSC_ERR_ARG): make a context's first call
+// outside any capture.
+static int scratch_address(cudaStream_t s, double **out)
 {
-    __shared__ double red[8];
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += Pn[b];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
-        *out = sqrt(t);
+    CtxGetCurrentFn f_cur;
+    CtxGetIdFn f_id;
+    if (!driver_calls(&f_cur, &f_id)) return SVDSC_ERR_CUDA;
+    CUcontext ctx = nullptr;
+    if (f_cur(&ctx) != CUDA_SUCCESS) return SVDSC_ERR_CUDA;
+    if (!ctx) {  // no context yet: the runtime creates the device's primary context on first use
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_cgs2_scratch) != cudaSuccess || !p) return SVDSC_ERR_CUDA;
+        if (f_cur(&ctx) != CUDA_SUCCESS || !ctx) return SVDSC_ERR_CUDA;
     }
+    unsigned long long id = 0;
+    if (f_id(ctx, &id) != CUDA_SUCCESS) return SVDSC_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    void *p = g_scratch_addr.find(id);
+    if (!p) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return SVDSC_ERR_CUDA;
+        if (cs != cudaStreamCaptureStatusNone) return SVDSC_ERR_ARG;
+        if (cudaGetSymbolAddress(&p, g_cgs2_scratch) != cudaSuccess || !p) return SVDSC_ERR_CUDA;
+        g_scratch_addr.put(id, p);
+    }
+    *out = (double *)p;
+    return SVDSC_OK;
 }
 
 }  // namespace svdsc
@@ -73,13 +100,13 @@ extern "C" int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, i
     if (ncols > kNoAllocMaxCols) return SVDSC_ERR_SIZE;
     const Chunk ch = make_chunk(len, 2 * 152);
     if (ch.nb > kNoAllocMaxChunks || ch.nbu > kNoAllocMaxNormParts) return SVDSC_ERR_SIZE;
+    cudaStream_t s = (cudaStream_t)stream;
     double *base = nullptr;
-    int rc = scratch_address(&base);
+    int rc = scratch_address(s, &base);
     if (rc != SVDSC_OK) return rc;
     double *P = base;
     double *h = base + (size_t)kNoAllocMaxChunks * kNoAllocMaxCols;
     double *Pn = h + kNoAllocMaxCols;
-    cudaStream_t s = (cudaStream_t)stream;
     // every scratch element read below is written first in the same call, so
     // nothing left by an earlier call needs clearing
     if (ncols > 0) {
@@ -91,6 +118,6 @@ extern "C" int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, i
     } else {
         norm_partial(w, ch, Pn, nullptr, s);
     }
-    noalloc_norm_kernel<<<1, 256, 0, s>>>(Pn, ch.nbu, norm_out);
+    norm_from_partials(Pn, ch.nbu, norm_out, s);
     return cudaGetLastError() == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
 }

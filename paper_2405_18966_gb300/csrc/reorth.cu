@@ -400,6 +400,28 @@ void norm_partial(const double *w, const Chunk &c, double *Pn, const int *poison
     norm_partial_kernel<<<c.nbu, kRowThreads, 0, s>>>(w, c.len, c.Ru, Pn, poison);
 }
 
+// *out = sqrt(sum of the nb partial sums of ||w||^2), in a fixed order (one CTA).
+__global__ void __launch_bounds__(256)
+norm_from_partials_kernel(const double *__restrict__ Pn, int nb, double *out)
+{
+    __shared__ double red[8];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += Pn[b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        *out = sqrt(t);
+    }
+}
+
+void norm_from_partials(const double *Pn, int nb, double *out, cudaStream_t s)
+{
+    norm_from_partials_kernel<<<1, 256, 0, s>>>(Pn, nb, out);
+}
+
 // ---------------------------------------------------------------- finalize
 
 __global__ void __launch_bounds__(kRowThreads)

@@ -11,128 +11,7 @@
 #include <cstring>
 #include <vector>
 #include <nvtx3/nvToolsExt.h>
-#include "internal.cuh"
-
-using namespace svdsc;
-
-struct StepRec {
-    int side;    // 0: u (column of U), 1: v (column of V)
-    int col;     // column index created
-    int parity;  // anorm parity used by its finalize
-};
-
-struct svdsc_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int precision = SVDSC_FP64;
-    uint64_t seed = 0;
-    int format = SVDSC_CSR;
-    int64_t m = 0, n = 0;
-    DevCSR A, AT;
-    DevDense D;
-    double *dense_part = nullptr;
-    Chunk cm, cn;
-    // workspace sized for t_cap
-    int t_cap = 0;
-    int64_t ldu = 0, ldv = 0;
-    double *U = nullptr, *V = nullptr, *T = nullptr;
-    float *U32 = nullptr, *V32 = nullptr;
-    // second bases: the tensor-core restart GEMM writes out of place and the
-    // two sets swap roles at every restart
-    double *Ua = nullptr, *Va = nullptr;
-    float *U32a = nullptr, *V32a = nullptr;
-    void *gemm_ws = nullptr;
-    int restart_gemm = 0;
-    int which = 0;  // 0: k largest triplets, 1: k smallest
-    int reorth = 0; // 0: CGS2 on every Lanczos vector, 1: partial (estimate-driven)
-    double *mu = nullptr, *nu = nullptr;  // partial re-orthogonalization estimates (t + 2 each)
-    PrState *pr = nullptr;
-    int pr_kk = 0;  // size of the last augmented restart (spike column kk + 1 of T), 0 before
-    double *P = nullptr, *h = nullptr, *Pn = nullptr;
-    double *Sh = nullptr, *Uh = nullptr, *Vh = nullptr, *res = nullptr, *rho = nullptr;
-    SvdWork svd;
-    DevStatus *st = nullptr;
-    DevStatus *st_host = nullptr;  // pinned
-    // per-solve state
-    int64_t launches = 0;
-    int parity = 0;
-    int t = 0, k = 0;
-    uint64_t draws = 0;
-    int breakdowns = 0;
-    int64_t n_matvec = 0, n_steps = 0;
-    std::vector<StepRec> steps;
-    // per-phase accounting (svdsc_info.ms / launches / bytes / flops)
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-    struct Rec { int ph, e0, e1; };
-    std::vector<Rec> recs;
-    int64_t ph_launch[SVDSC_NUM_PHASES] = {0};
-    double ph_bytes[SVDSC_NUM_PHASES] = {0};
-    double ph_flops[SVDSC_NUM_PHASES] = {0};
-};
-
-static int next_event(svdsc_ctx *c)
-{
-    if (c->ev_used == c->ev_pool.size()) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return -1;
-        c->ev_pool.push_back(e);
-    }
-    return (int)c->ev_used++;
-}
-
-// Opens a timed region on the stream (returns -1 when timing is off).
-static int ph_begin(svdsc_ctx *c)
-{
-    if (!c->timing) return -1;
-    const int e = next_event(c);
-    if (e >= 0) cudaEventRecord(c->ev_pool[e], c->stream);
-    return e;
-}
-
-static void ph_end(svdsc_ctx *c, int ph, int e0, int nlaunch, double bytes, double flops)
-{
-    c->ph_launch[ph] += nlaunch;
-    c->ph_bytes[ph] += bytes;
-    c->ph_flops[ph] += flops;
-    c->launches += nlaunch;
-    if (e0 < 0) return;
-    const int e1 = next_event(c);
-    if (e1 < 0) return;
-    cudaEventRecord(c->ev_pool[e1], c->stream);
-    c->recs.push_back({ph, e0, e1});
-}
-
-static void ph_reset(svdsc_ctx *c)
-{
-    c->ev_used = 0;
-    c->recs.clear();
-    for (int i = 0; i < SVDSC_NUM_PHASES; i++) {
-        c->ph_launch[i] = 0;
-        c->ph_bytes[i] = 0.0;
-        c->ph_flops[i] = 0.0;
-    }
-}
-
-#define CU(x)                                          \
-    do {                                               \
-        cudaError_t e_ = (x);                          \
-        if (e_ != cudaSuccess) return SVDSC_ERR_CUDA;  \
-    } while (0)
-
-// Named ranges for Nsight Systems timelines (no-ops unless a tool is attached).
-struct NvtxRange {
-    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
-    ~NvtxRange() { nvtxRangePop(); }
-};
-
-static inline double *colU(svdsc_ctx *c, int j) { return c->U + (int64_t)j * c->ldu; }
-static inline double *colV(svdsc_ctx *c, int j) { return c->V + (int64_t)j * c->ldv; }
-static inline float *colU32(svdsc_ctx *c, int j) { return c->U32 ? c->U32 + (int64_t)j * c->ldu : nullptr; }
-static inline float *colV32(svdsc_ctx *c, int j) { return c->V32 ? c->V32 + (int64_t)j * c->ldv : nullptr; }
-static inline double *Tent(svdsc_ctx *c, int r, int col) { return c->T + r + (int64_t)col * (c->t + 1); }
-static inline int *poison_ptr(svdsc_ctx *c) { return &c->st->poison; }
+#include "context.cuh"
 
 // ----------------------------------------------------------- small kernels
 
@@ -276,8 +155,8 @@ static int gemm_inplace(svdsc_ctx *c, double *W, int64_t ld, int64_t rows, int t
 
 // Out-of-place tensor-core update C = W Q (svdsc_gemm modes): FP64 digits, or
 // three BF16 pieces of the FP32 shadow in the mixed form (C32 gets the shadow).
-static int gemm_tc(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, int64_t rows, int t,
-                   const double *Q, int k, double *C, float *C32)
+int gemm_tc(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, int64_t rows, int t,
+            const double *Q, int k, double *C, float *C32)
 {
     const int mode = (c->precision == SVDSC_MIXED) ? 1 : 0;
     const int e0 = ph_begin(c);
@@ -329,21 +208,6 @@ sign_kernel(double *__restrict__ U, int64_t ldu, int64_t m, double *__restrict__
     for (int64_t r = threadIdx.x; r < m; r += blockDim.x) u[r] = -u[r];
 }
 
-__global__ void sum_sqrt_kernel(const double *__restrict__ Pn, int nb, double *out)
-{
-    __shared__ double red[8];
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += Pn[b];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
-        *out = sqrt(t);
-    }
-}
-
 __global__ void check_finite_kernel(const double *__restrict__ a, int64_t ld, int64_t m, int64_t n,
                                     int *bad)
 {
@@ -377,9 +241,10 @@ static void free_workspace(svdsc_ctx *c)
     c->svd.rot = nullptr;
     c->svd.bar = nullptr;
     c->t_cap = 0;
+    block_free(c);
 }
 
-static int reserve_ws(svdsc_ctx *c, int t)
+int reserve_ws(svdsc_ctx *c, int t)
 {
     if (t <= c->t_cap) return SVDSC_OK;
     cudaStreamSynchronize(c->stream);
@@ -497,6 +362,12 @@ static void cgs2(svdsc_ctx *c, const double *W, const float *W32, int64_t ld, in
     }
 }
 
+// CGS2 in FP64 against ncols columns (partial sums of ||w||^2 left in c->Pn).
+void cgs2_fp64(svdsc_ctx *c, const double *W, int64_t ld, int ncols, double *w, const Chunk &ch)
+{
+    cgs2(c, W, nullptr, ld, ncols, w, ch, nullptr);
+}
+
 static void do_finalize(svdsc_ctx *c, int side, int col, double *T_entry, int mode)
 {
     const Chunk &ch = side == 0 ? c->cm : c->cn;
@@ -578,7 +449,7 @@ static int issue_segment(svdsc_ctx *c, int s, bool first_u)
     return SVDSC_OK;
 }
 
-static int read_status(svdsc_ctx *c)
+int read_status(svdsc_ctx *c)
 {
     CU(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -708,6 +579,11 @@ int svdsc_create(svdsc_ctx **out, const svdsc_matrix *A, const svdsc_options *op
         (c->which == SVDSC_SMALLEST && A->m < A->n)) { delete c; return SVDSC_ERR_ARG; }
     c->reorth = opt ? opt->reorth : SVDSC_REORTH_FULL;
     if (c->reorth != SVDSC_REORTH_FULL && c->reorth != SVDSC_REORTH_PARTIAL) { delete c; return SVDSC_ERR_ARG; }
+    c->block = (opt && opt->block > 1) ? opt->block : 1;
+    if (opt && opt->block < 0) { delete c; return SVDSC_ERR_ARG; }
+    if (c->block > 1 && ((c->block != 2 && c->block != 4 && c->block != 8 && c->block != 16) ||
+                         A->format != SVDSC_CSR || c->which != SVDSC_LARGEST || c->reorth != SVDSC_REORTH_FULL ||
+                         c->restart_gemm != 0)) { delete c; return SVDSC_ERR_ARG; }
     c->format = A->format;
     c->m = A->m;
     c->n = A->n;
@@ -804,6 +680,13 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     }
     CU(cudaMemsetAsync(c->T, 0, sizeof(double) * (size_t)(t + 1) * (t + 1), s));
 
+    int restarts = 0;
+    double *Uo = c->U, *Vo = c->V;
+    DevStatus fin;
+    if (c->block > 1) {
+        rc = solve_block(c, k, p, tol, maxit, v0, v0_on_device, &Uo, &Vo, &restarts, &fin);
+        if (rc) return rc;
+    } else {
     // Alg. 1, start: v_1 (the caller's v0 or draw 0), normalised
     if (v0) CU(cudaMemcpyAsync(colV(c, 0), v0, sizeof(double) * c->n,
                                v0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -840,7 +723,6 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     rc = settle(c);
     if (rc) return rc;
 
-    int restarts = 0;
     for (int it = 1; it <= maxit; it++) {
         // Alg. 2: SVD of T(1:t,1:t)
         {
@@ -924,11 +806,10 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         rc = settle(c);
         if (rc) return rc;
     }
-    const DevStatus fin = *c->st_host;
+    fin = *c->st_host;
 
     // outputs of Alg. 2 (into the spare bases or in place, then copied out)
     NvtxRange out_range("svdsc: outputs");
-    double *Uo = c->U, *Vo = c->V;
     if (c->restart_gemm == 0) {
         rc = gemm_tc(c, c->U, c->U32, c->ldu, c->m, t, c->Uh, k, c->Ua, nullptr);
         if (rc) return rc;
@@ -942,6 +823,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         rc = gemm_inplace(c, c->V, c->ldv, c->n, t, c->Vh, k);
         if (rc) return rc;
     }
+    }  // single-vector form
     sign_kernel<<<k, 256, 0, s>>>(Uo, c->ldu, c->m, Vo, c->ldv, c->n);
     ph_end(c, SVDSC_PH_OTHER, -1, 1, 0.0, 0.0);
     CU(cudaGetLastError());
@@ -953,7 +835,10 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
     CU(cudaMemcpy2DAsync(V, sizeof(double) * ldv, Vo, sizeof(double) * c->ldv, sizeof(double) * c->n, k,
                          kind, s));
     CU(cudaStreamSynchronize(s));
-    if (c->st_host->timeout || read_status(c) != SVDSC_OK || c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
+    if (c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
+    rc = read_status(c);  // a CUDA error here is reported as such, not as a timeout
+    if (rc) return rc;
+    if (c->st_host->timeout) return SVDSC_ERR_TIMEOUT;
     if (info) {
         memset(info, 0, sizeof(*info));
         info->converged = fin.converged;
@@ -965,7 +850,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         info->n_launches = c->launches;
         info->anorm_est = std::max(fin.anorm[0], fin.anorm[1]);
         info->beta_t = fin.beta_t;
-        info->t = t;
+        info->t = c->block > 1 ? c->t : t;
         for (int i = 0; i < SVDSC_NUM_PHASES; i++) {
             info->launches[i] = c->ph_launch[i];
             info->bytes[i] = c->ph_bytes[i];
@@ -973,7 +858,7 @@ int svdsc_solve(svdsc_ctx *c, int k, int p, double tol, int maxit, const double 
         }
         // every Lanczos vector but u_1 (full), or the estimate-driven ones plus
         // the restart vectors (partial), whose CGS2 bytes were counted on the device
-        info->n_reorth = c->n_steps - 1;
+        info->n_reorth = c->n_steps - c->block;
         if (c->reorth) {
             PrState ps;
             CU(cudaMemcpy(&ps, c->pr, sizeof(PrState), cudaMemcpyDeviceToHost));
@@ -1018,7 +903,7 @@ int svdsc_cgs2(svdsc_ctx *c, int64_t len, int64_t ncols, const double *W, int64_
     if (!ch) return SVDSC_ERR_ARG;
     if (ncols > c->t_cap + 1) return SVDSC_ERR_SIZE;
     cgs2(c, W, nullptr, ldw, (int)ncols, w, *ch, nullptr);
-    sum_sqrt_kernel<<<1, 256, 0, c->stream>>>(c->Pn, ch->nbu, norm_out);
+    norm_from_partials(c->Pn, ch->nbu, norm_out, c->stream);
     if (cudaGetLastError() != cudaSuccess) return SVDSC_ERR_CUDA;
     return cudaStreamSynchronize(c->stream) == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
 }

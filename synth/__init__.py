@@ -282,19 +282,40 @@ class BatchItem:
     p: int
 
 
-def workload_batch(count: int = 256, seed: int = BASE_SEED + 5, size_scale: float = 1.0) -> list:
+def workload_batch(count: int = 256, seed: int = BASE_SEED + 5, size_scale: float = 1.0,
+                   only=None) -> list:
     """`count` CSR matrices: m ~ U{2000..60000}, n ~ U{1000..30000}, row lengths
     ~ U{5..50}, values N(0,1) FP32; k ~ U{5..40}, p = k (sizes multiplied by
-    `size_scale` for quick tests)."""
+    `size_scale` for quick tests).  `only` (indices): build just those items
+    of the same batch (the shape and seed draws of the others are still taken,
+    so item i is identical either way); returns them in the order given."""
     rng = np.random.default_rng(seed)
-    items = []
+    want = None if only is None else set(int(i) for i in only)
+    items = {}
     for b in range(count):
         m = int(rng.integers(2000, 60001) * size_scale)
         n = int(rng.integers(1000, 30001) * size_scale)
         k = int(rng.integers(5, 41))
         m = max(m, 2 * k + 2)
         n = max(n, 2 * k + 2)
-        a = csr_uniform_rows(m, n, 5, 50, int(rng.integers(0, 2**62)), dtype=np.float32,
-                             name=f"batch{b}-{m}x{n}")
-        items.append(BatchItem(a, k, k))
-    return items
+        mseed = int(rng.integers(0, 2**62))
+        if want is not None and b not in want:
+            continue
+        a = csr_uniform_rows(m, n, 5, 50, mseed, dtype=np.float32, name=f"batch{b}-{m}x{n}")
+        items[b] = BatchItem(a, k, k)
+    if only is None:
+        return [items[b] for b in range(count)]
+    return [items[int(i)] for i in only]
+
+
+def workload_batch_shapes(count: int = 256, seed: int = BASE_SEED + 5, size_scale: float = 1.0) -> list:
+    """(m, n, k) of every item of workload_batch, without building the matrices."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(rng.integers(2000, 60001) * size_scale)
+        n = int(rng.integers(1000, 30001) * size_scale)
+        k = int(rng.integers(5, 41))
+        rng.integers(0, 2**62)
+        out.append((max(m, 2 * k + 2), max(n, 2 * k + 2), k))
+    return out

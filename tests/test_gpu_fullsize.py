@@ -94,16 +94,18 @@ def test_mixed_k100_sigma_errors_reported_per_triplet(pkg, orc):
 
 
 def test_batch_full_size_sampled(pkg, orc):
-    """The 256-matrix batch (one persistent launch): all converge; sampled matrices
-    against the FP64 oracle (sigma within 1e-6)."""
+    """The 256-matrix batch (one persistent launch): all converge; five matrices
+    sampled across the batch's sizes (the smallest, the quartiles and the
+    largest by nonzeros) against the FP64 oracle: sigma within 1e-6, every
+    vector within its gap-scaled angle, every triplet's residual."""
+    from test_gpu_batched import check_vs_oracle
     items = synth.workload_batch()
     b = pkg.Batch([it.a for it in items], [it.k for it in items], seed=1)
     out = b.solve(1e-10, 1000)
     assert sum(i["converged"] for i in out["infos"]) == len(items)
-    small = sorted(range(len(items)), key=lambda i: items[i].a.nnz)[:3]
-    for i in small:
+    by_nnz = sorted(range(len(items)), key=lambda i: items[i].a.nnz)
+    sample = [by_nnz[int(q * (len(items) - 1))] for q in (0.0, 0.25, 0.5, 0.75, 1.0)]
+    for i in sample:
         it = items[i]
-        a64 = synth.CSR(it.a.m, it.a.n, it.a.row_ptr, it.a.col_idx, it.a.values.astype(np.float64))
-        ref = orc.svds(a64, it.k, it.k, 1e-10, 1000, seed=1)
-        assert np.max(np.abs(out["S"][i] - ref["S"]) / ref["S"]) <= 1e-6
+        check_vs_oracle(orc, it.a, it.k, out["S"][i], out["U"][i], out["V"][i])
     b.close()

@@ -112,3 +112,15 @@ def test_binding_struct_layouts_match_the_header(struct, cls, tmp_path):
     assert ctypes.sizeof(C) == lay["size"], (ctypes.sizeof(C), lay["size"])
     for f in fields:
         assert getattr(C, f).offset == lay[f], (f, getattr(C, f).offset, lay[f])
+
+
+def test_noalloc_address_table_is_keyed_by_context(tmp_path):
+    """svdsc_cgs2_noalloc remembers its scratch array's device address per CUDA
+    context ID (a device reset or a second context places the array anew);
+    the table's keying is checked here in plain C++ without a GPU."""
+    exe = tmp_path / "ctx_cache_test"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-Wall", "-Werror",
+                    "-I", os.path.join(ROOT, "paper_2405_18966_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "c", "ctx_cache_test.cpp"), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and "OK (0 failures)" in r.stdout, r.stdout
