@@ -539,13 +539,13 @@ __global__ void brepair_accum_kernel(const double *__restrict__ h, int c0, int l
     for (int i = threadIdx.x; i < l; i += blockDim.x) Rcc[i + l * B] += h[c0 + i];
 }
 
-__global__ void brepair_norm_kernel(double *__restrict__ w, int64_t len, const double *__restrict__ nrm2,
+__global__ void brepair_norm_kernel(double *__restrict__ w, int64_t len, const double *__restrict__ nrm_in,
                                     int l, int B, double *__restrict__ Rcc, DevStatus *st, int parity,
                                     int *flag, int mode)
 {
     // mode 0: a Lanczos column (breakdown test against the ||A|| estimate);
-    // mode 1: a random replacement (needs norm > 1e-8)
-    const double nrm = sqrt(*nrm2);
+    // mode 1: a random replacement (needs norm > 1e-8).  *nrm_in = ||w||.
+    const double nrm = *nrm_in;
     const double anorm = st->anorm[parity];
     const bool ok = mode == 0 ? (nrm > 1e-13 * anorm && isfinite(nrm)) : (nrm > 1e-8 && isfinite(nrm));
     if (!ok) {
