@@ -395,17 +395,17 @@ def block_comparison(pkg, torch, A, k, p, tol, maxit, S_ref, blocks=(1, 4, 8, 16
             row = {"precision": prec, "block": b}
             try:
                 with pkg.Solver(A_p, precision=prec, block=b) as s:
-                    r = s.solve(k, p, tol, 1)  # first pass only: sizes the workspace
+                    r = s.solve(k, p, tol, 1, out="device")  # first pass only: sizes the workspace
                     torch.cuda.synchronize()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record()
-                    r = s.solve(k, p, tol, maxit)
+                    r = s.solve(k, p, tol, maxit, out="device")  # outputs stay on the device
                     e1.record()
                     torch.cuda.synchronize()
                     sec = e0.elapsed_time(e1) / 1e3
                 inf = r.info
                 by = sum(inf["bytes"][ph] for ph in ("spmv", "gemv_t", "gemv_n"))
-                S = np.asarray(r.S)
+                S = r.S.cpu().numpy()
                 row.update({"seconds": sec, "restarts": inf["restarts"], "converged": inf["converged"],
                             "n_matvec": inf["n_matvec"], "t_last": inf["t"], "launches": inf["n_launches"],
                             "spmv_reorth_bytes": by, "alg_gbs_over_solve": by / sec / 1e9,

@@ -320,9 +320,9 @@ int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, int64_t ldw,
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent truncated SVDs (uneven shapes and k) solved
- * in ONE persistent kernel launch, replayed from a CUDA graph.  Thread-block
- * clusters (1-8 CTAs, see svdsc_batch_layout) take matrices from a work queue
- * (largest estimated cost first) and run Alg. 2 for each from start to finish.  Precision is the mixed form (FP32
+ * in ONE persistent kernel launch, replayed from a CUDA graph.
+ * Thread-block clusters (1-8 CTAs) take matrices from a work queue (largest
+ * estimated cost first) and run Alg. 2 for each from start to finish.  Precision is the mixed form (FP32
  * CSR values, FP32 SpMV and first CGS pass, FP64 second pass, norms, projected
  * SVD and residual test, FP32 restart GEMM); options.precision must be
  * SVDSC_MIXED.  Limits per matrix: CSR input, 1 <= k <= 48, t = k + p <= 80
@@ -356,8 +356,8 @@ int svdsc_batch_tuning(const svdsc_batch *b, int i, int *lanes_A, int *lanes_AT,
 /* CTAs per matrix (thread-block cluster size: the rows of A, A^T and of the
  * bases are split across them) and the number of clusters of the persistent
  * launch.  Automatic choice: the smallest power of two <= 8 for which the
- * costliest matrix, run on one cluster, takes at most its share of the
- * batch's estimated work. */
+ * costliest matrix (estimated by the cost of one Lanczos pass), run on one
+ * cluster, takes at most its share of the batch's estimated work. */
 int svdsc_batch_layout(const svdsc_batch *b, int *cluster_size, int *clusters);
 
 /* Per-matrix profile of the last batch solve (arrays of nb entries, each may

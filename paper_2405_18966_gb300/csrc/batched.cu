@@ -65,7 +65,7 @@ struct BSlot {   // one per cluster (bases), T one per CTA
 
 struct BParams {
     double tol;
-    int maxit, nb;
+    int maxit, pad;
 };
 
 // ------------------------------------------------------------ cluster helpers
@@ -128,6 +128,11 @@ __device__ __forceinline__ int cl_ld_i32(const int *p, uint32_t rank)
 // shared-memory layout (doubles)
 constexpr int kSmB = 0;                               // B: t x t (Jacobi columns)
 constexpr int kSmW = kSmB + kBMaxT * kBMaxT;          // W: t x t (rotations)
+// The sparse products gather from a copy of the whole input vector (FP32) in
+// shared memory when it fits in B and W, which only the projected SVD uses
+// (never during a product).  (A larger dedicated region was measured slower:
+// it shrinks the L1 cache that the gathers of longer vectors rely on.)
+constexpr int kXCap = 2 * (2 * kBMaxT * kBMaxT);      // 25,600 floats
 constexpr int kSmS = kSmW + kBMaxT * kBMaxT;          // sorted sigma (t)
 constexpr int kSmUt = kSmS + kBMaxT;                  // Uh(t, j) for j < k
 constexpr int kSmRho = kSmUt + kBMaxT;                // rho (k)
@@ -185,10 +190,22 @@ __device__ void cta_spmv_g(const int64_t *__restrict__ rp, const int32_t *__rest
     }
 }
 
-// y = A x - coef z with FP32 values, FP32 x and FP32 accumulation
+// y = A x - coef z with FP32 values, FP32 x and FP32 accumulation.  When the
+// whole x (xlen entries, 16-byte aligned) fits in the staging region xs, the
+// CTA first copies it there, so every gather is a shared-memory load; else
+// the gathers go to L1 / L2.  (Splitting a longer x across the cluster's
+// shared memory, gathered with ld.shared::cluster, measured slower than the
+// L2 gathers: 16.1 s against 12.5 s for the 256-matrix batch.)
 __device__ void cta_spmv(int G, const int64_t *rp, const int32_t *col, const float *val, const float *x,
-                         int64_t rows, const double *z, double coef, double *y)
+                         int64_t xlen, float *xs, int64_t rows, const double *z, double coef, double *y)
 {
+    if (xs && xlen <= kXCap) {
+        const int64_t n4 = xlen >> 2;
+        for (int64_t j = threadIdx.x; j < n4; j += kBT) ((float4 *)xs)[j] = ((const float4 *)x)[j];
+        for (int64_t j = 4 * n4 + threadIdx.x; j < xlen; j += kBT) xs[j] = x[j];
+        __syncthreads();
+        x = xs;
+    }
     switch (G) {
     case 1: cta_spmv_g<1>(rp, col, val, x, rows, z, coef, y); break;
     case 2: cta_spmv_g<2>(rp, col, val, x, rows, z, coef, y); break;
@@ -350,6 +367,7 @@ struct BRun {
     double anorm;
     double *sm;
     float *smf;
+    float *xs;                 // staging region of the products' input vector
     bool failed;
     bool lead;                 // rank 0 of the cluster writes the per-matrix outputs
     long long cyc[5];          // SM cycles per phase (see BStat::cycles_phase)
@@ -467,7 +485,7 @@ __device__ void lbp_from(BRun &R, int s)
         // v_{i+1} = A^T u_i - alpha_i v_i, CGS2 against v_1..v_i
         double *vout = R.V + (int64_t)i * R.ldv;
         long long c0 = clock64();
-        cta_spmv(M.gAT, M.rpT + R.n0, M.colT, M.valT, R.U32 + (int64_t)(i - 1) * R.ldu, R.n1 - R.n0,
+        cta_spmv(M.gAT, M.rpT + R.n0, M.colT, M.valT, R.U32 + (int64_t)(i - 1) * R.ldu, R.m, R.xs, R.n1 - R.n0,
                  R.V + (int64_t)(i - 1) * R.ldv + R.n0, *Tb(R, i - 1, i - 1), vout + R.n0);
         R.cyc[0] += clock64() - c0;
         double n2 = cl_cgs2(R, R.V, R.V32, R.ldv, i, vout, R.n0, R.n1);
@@ -481,7 +499,7 @@ __device__ void lbp_from(BRun &R, int s)
         // u_{i+1} = A v_{i+1} - beta_i u_i, CGS2 against u_1..u_i
         double *uout = R.U + (int64_t)i * R.ldu;
         c0 = clock64();
-        cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32 + (int64_t)i * R.ldv, R.m1 - R.m0,
+        cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32 + (int64_t)i * R.ldv, R.n, R.xs, R.m1 - R.m0,
                  R.U + (int64_t)(i - 1) * R.ldu + R.m0, beta, uout + R.m0);
         R.cyc[0] += clock64() - c0;
         n2 = cl_cgs2(R, R.U, R.U32, R.ldu, i, uout, R.m0, R.m1);
@@ -495,7 +513,7 @@ __device__ void lbp_from(BRun &R, int s)
 }
 
 // Projected SVD of T(1:t,1:t) by one-sided Jacobi in shared memory (FP64,
-// round-robin pairs, one warp per pair), computed by every CTA of the cluster
+// round-robin pairs, eight lanes per pair), computed by every CTA of the cluster
 // on identical input.  Leaves the descending sigma in sm[kSmS], Uh(t, j) in
 // sm[kSmUt] and the leading k columns of Uh and Vh (as FP32) in the Q buffers.
 __device__ void cta_small_svd(BRun &R)
@@ -505,6 +523,9 @@ __device__ void cta_small_svd(BRun &R)
     float *QU = R.smf + kSmQU, *QV = R.smf + kSmQV;
     __shared__ int rot_count;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kLP = 8;  // lanes per column pair (t <= 80: at most 40 pairs, 64 groups)
+    const int grp = threadIdx.x / kLP, gl = threadIdx.x % kLP;
+    const unsigned gmask = 0xFFu << (lane & ~(kLP - 1));
     for (int i = threadIdx.x; i < t * t; i += kBT) {
         const int r = i % t, c = i / t;
         B[r + c * t] = *Tb(R, r, c);
@@ -520,35 +541,37 @@ __device__ void cta_small_svd(BRun &R)
         __syncthreads();
         sweeps++;
         for (int round = 0; round < n2 - 1; round++) {
-            for (int slot = warp; slot < n2 / 2; slot += kBW) {
+            // one group of kLP lanes per pair: every pair of the round is in flight at once
+            for (int slot = grp; slot < n2 / 2; slot += kBT / kLP) {
                 auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (n2 - 1)) + 1; };
                 int p = player(slot), q = player(n2 - 1 - slot);
                 if (p > q) { const int x = p; p = q; q = x; }
                 if (q >= t) continue;
                 double *bp = B + p * t, *bq = B + q * t;
                 double a = 0.0, b = 0.0, g = 0.0;
-                for (int r = lane; r < t; r += 32) {
+                for (int r = gl; r < t; r += kLP) {
                     a += bp[r] * bp[r];
                     b += bq[r] * bq[r];
                     g += bp[r] * bq[r];
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    b += __shfl_xor_sync(0xffffffffu, b, o);
-                    g += __shfl_xor_sync(0xffffffffu, g, o);
+#pragma unroll
+                for (int o = kLP / 2; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(gmask, a, o);
+                    b += __shfl_xor_sync(gmask, b, o);
+                    g += __shfl_xor_sync(gmask, g, o);
                 }
                 if (g == 0.0 || fabs(g) <= tol * sqrt(a * b)) continue;
                 const double zeta = (b - a) / (2.0 * g);
                 const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                 const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-                if (lane == 0) atomicAdd(&rot_count, 1);
-                for (int r = lane; r < t; r += 32) {
+                if (gl == 0) atomicAdd(&rot_count, 1);
+                for (int r = gl; r < t; r += kLP) {
                     const double x = bp[r], y = bq[r];
                     bp[r] = c * x - s * y;
                     bq[r] = s * x + c * y;
                 }
                 double *wp = Wm + p * t, *wq = Wm + q * t;
-                for (int r = lane; r < t; r += 32) {
+                for (int r = gl; r < t; r += kLP) {
                     const double x = wp[r], y = wq[r];
                     wp[r] = c * x - s * y;
                     wq[r] = s * x + c * y;
@@ -681,6 +704,7 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
     R.anorm = 0.0;
     R.sm = sm;
     R.smf = smf;
+    R.xs = (float *)(sm + kSmB);
     R.failed = false;
     for (int q = 0; q < 5; q++) R.cyc[q] = 0;
     double *red = sm + kSmRed;
@@ -703,7 +727,7 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
         cl_sync();
     }
     // u_1 = A v_1, alpha_1
-    cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32, R.m1 - R.m0, nullptr, 0.0, R.U + R.m0);
+    cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32, R.n, R.xs, R.m1 - R.m0, nullptr, 0.0, R.U + R.m0);
     {
         const double a1 = finish_vector(R, 0, 0, cl_sum_scalar(R, cta_norm2(R.U + R.m0, R.m1 - R.m0, red)));
         if (threadIdx.x == 0) *Tb(R, 0, 0) = a1;
@@ -767,7 +791,8 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
         cl_sync();  // v_{k+1} complete on every CTA before the product reads it
         // u_{k+1} = A v_{k+1} - U~ rho (Eq. 7), CGS2 against U~
         double *uk = R.U + (int64_t)k * R.ldu;
-        cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32 + (int64_t)k * R.ldv, R.m1 - R.m0, nullptr, 0.0, uk + R.m0);
+        cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32 + (int64_t)k * R.ldv, R.n, R.xs, R.m1 - R.m0, nullptr, 0.0,
+                 uk + R.m0);
         cta_update<double, double>(R.U + R.m0, R.ldu, k, rho, uk + R.m0, R.m1 - R.m0, false, red);
         const double n2 = cl_cgs2(R, R.U, R.U32, R.ldu, k, uk, R.m0, R.m1);
         const double ak = finish_vector(R, 0, k, n2);
@@ -800,9 +825,11 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
     phase = R.phase;
 }
 
+// The work queue: order[0..n) are matrix ids, largest estimated cost first;
+// *next is the next position to take.
 __global__ void __launch_bounds__(kBT, 1)
-batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, BStat *stats,
-               const BSlot *__restrict__ slots, double *Tall, int64_t tstride, const BParams *prm, int *queue)
+batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, int n, int *next, BStat *stats,
+               const BSlot *__restrict__ slots, double *Tall, int64_t tstride, const BParams *prm)
 {
     extern __shared__ __align__(16) double bsm[];
     double *sm = bsm;
@@ -815,13 +842,15 @@ batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, BSt
     while (true) {
         __syncthreads();
         cl_sync();  // every CTA has read the previous item
-        if (threadIdx.x == 0 && cl_rank() == 0) item = atomicAdd(queue, 1);
+        if (threadIdx.x == 0 && cl_rank() == 0) {
+            const int i = atomicAdd(next, 1);
+            item = i < n ? order[i] : -1;
+        }
         __syncthreads();
         cl_sync();
-        const int it = cl_ld_i32(&item, 0);
+        const int b = cl_ld_i32(&item, 0);
         cl_sync();  // no CTA leaves while another still reads its shared memory
-        if (it >= P.nb) break;
-        const int b = order[it];
+        if (b < 0) break;
         solve_one(mats[b], stats + b, slot, Tpriv, P, sm, smf, phase);
     }
 }
@@ -830,11 +859,12 @@ batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, BSt
 // Times each candidate on one CTA per SM, all running the same product of the
 // class representative (the per-SM throughput the persistent kernel sees).
 __global__ void __launch_bounds__(kBT, 1)
-tune_spmv_kernel(const int64_t *rp, const int32_t *col, const float *val, const float *x, int64_t rows,
+tune_spmv_kernel(const int64_t *rp, const int32_t *col, const float *val, const float *x, int64_t xlen, int64_t rows,
                  double *y_slots, int64_t ldy, int G, int reps)
 {
+    extern __shared__ __align__(16) double bsm[];
     double *y = y_slots + (int64_t)blockIdx.x * ldy;
-    for (int r = 0; r < reps; r++) cta_spmv(G, rp, col, val, x, rows, nullptr, 0.0, y);
+    for (int r = 0; r < reps; r++) cta_spmv(G, rp, col, val, x, xlen, (float *)bsm, rows, nullptr, 0.0, y);
 }
 
 __global__ void __launch_bounds__(kBT, 1)
@@ -851,24 +881,30 @@ tune_proj_kernel(const double *W_slots, int64_t ldw_slot, int64_t ld, int ncols,
 // ============================================================ host side
 using namespace svdsc;
 
+// One persistent launch: its cluster size, clusters (one workspace slot
+// each, sized for the largest matrix) and a private projected matrix per CTA.
+struct BLaunch {
+    int csize = 0;
+    int nslots = 0;
+    void *slot_mem = nullptr;
+    BSlot *d_slots = nullptr;
+    double *d_T = nullptr;
+};
+
 struct svdsc_batch {
     int nb = 0;
-    int nslots = 0;
     cudaStream_t stream = nullptr;
     std::vector<DevCSR> A, AT;
     std::vector<BMat> hm;        // host copy of the descriptors
     BMat *h_mats = nullptr;      // pinned staging copy (graph memcpy source)
     BParams *h_prm = nullptr;    // pinned
     BMat *d_mats = nullptr;
-    int *d_order = nullptr;
     BStat *d_stats = nullptr;
-    BSlot *d_slots = nullptr;
     BParams *d_prm = nullptr;
-    int *d_queue = nullptr;
-    void *slot_mem = nullptr;
-    double *d_T = nullptr;       // one projected matrix per CTA
+    int *d_order = nullptr;      // matrix ids, largest estimated cost first
+    int *d_next = nullptr;       // next queue position
     int64_t tstride = 0;
-    int csize = 1;               // CTAs per cluster (per matrix)
+    BLaunch L;
     double *out_mem = nullptr;   // device outputs when the caller wants host outputs
     std::vector<size_t> out_off;
     cudaGraph_t graph = nullptr;
@@ -919,8 +955,8 @@ static int tune_matrix(svdsc_batch *B, int b, int nsm, double *yscratch, int64_t
             double bt = 1e30;
             for (int G : cand) {
                 const double ms = time_ms(B->stream, [&] {
-                    tune_spmv_kernel<<<nsm, kBT, 0, B->stream>>>(C.row_ptr, C.col, C.val32, x32, C.m, yscratch, ldy,
-                                                                 G, 2);
+                    tune_spmv_kernel<<<nsm, kBT, sizeof(float) * kXCap, B->stream>>>(
+                        C.row_ptr, C.col, C.val32, x32, C.n, C.m, yscratch, ldy, G, 2);
                 });
                 B->tune_ms += 2 * ms;
                 if (ms < bt) { bt = ms; best = G; }
@@ -959,6 +995,14 @@ static int tune_matrix(svdsc_batch *B, int b, int nsm, double *yscratch, int64_t
 
 extern "C" {
 
+static void free_launch(BLaunch &L)
+{
+    cudaFree(L.slot_mem);
+    cudaFree(L.d_slots);
+    cudaFree(L.d_T);
+    L = BLaunch();
+}
+
 int svdsc_batch_destroy(svdsc_batch *B)
 {
     if (!B) return SVDSC_OK;
@@ -970,17 +1014,65 @@ int svdsc_batch_destroy(svdsc_batch *B)
     cudaFreeHost(B->h_mats);
     cudaFreeHost(B->h_prm);
     cudaFree(B->d_mats);
-    cudaFree(B->d_order);
     cudaFree(B->d_stats);
-    cudaFree(B->d_slots);
     cudaFree(B->d_prm);
-    cudaFree(B->d_queue);
-    cudaFree(B->slot_mem);
-    cudaFree(B->d_T);
+    cudaFree(B->d_order);
+    cudaFree(B->d_next);
+    free_launch(B->L);
     cudaFree(B->out_mem);
     if (B->stream) cudaStreamDestroy(B->stream);
     delete B;
     return SVDSC_OK;
+}
+
+static int max_clusters(int C)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C * 64);
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = kSmBytes;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, batched_kernel, &cfg) != cudaSuccess) return 0;
+    return ncl;
+}
+
+// Workspace of one launch: a slot (two sets of bases, FP64 and FP32) per
+// cluster, sized for the largest matrix, and a projected matrix per CTA.
+static int setup_launch(svdsc_batch *B, BLaunch &L, int64_t mmax, int64_t nmax, int tmax)
+{
+    const int64_t ldu = (mmax + 63) & ~int64_t(63), ldv = (nmax + 63) & ~int64_t(63);
+    const int64_t cols = tmax + 2;
+    const size_t per_slot = sizeof(double) * (size_t)(2 * ldu * cols + 2 * ldv * cols + 64) +
+                            sizeof(float) * (size_t)(2 * ldu * cols + 2 * ldv * cols + std::max(ldu, ldv)) + 4096;
+    std::vector<BSlot> slots(L.nslots);
+    if (cudaMalloc(&L.slot_mem, per_slot * L.nslots) != cudaSuccess) return SVDSC_ERR_NOMEM;
+    cudaMemsetAsync(L.slot_mem, 0, per_slot * L.nslots, B->stream);
+    if (cudaMalloc(&L.d_T, sizeof(double) * B->tstride * L.nslots * L.csize) != cudaSuccess) return SVDSC_ERR_NOMEM;
+    for (int s = 0; s < L.nslots; s++) {
+        uint8_t *base = (uint8_t *)L.slot_mem + per_slot * s;
+        auto take = [&](size_t bytes) { uint8_t *p = base; base += (bytes + 255) & ~(size_t)255; return p; };
+        BSlot &S = slots[s];
+        S.ldu = ldu; S.ldv = ldv;
+        S.U0 = (double *)take(sizeof(double) * ldu * cols);
+        S.U1 = (double *)take(sizeof(double) * ldu * cols);
+        S.V0 = (double *)take(sizeof(double) * ldv * cols);
+        S.V1 = (double *)take(sizeof(double) * ldv * cols);
+        S.U32_0 = (float *)take(sizeof(float) * ldu * cols);
+        S.U32_1 = (float *)take(sizeof(float) * ldu * cols);
+        S.V32_0 = (float *)take(sizeof(float) * ldv * cols);
+        S.V32_1 = (float *)take(sizeof(float) * ldv * cols);
+        S.wf = (float *)take(sizeof(float) * std::max(ldu, ldv));
+    }
+    if (cudaMalloc(&L.d_slots, sizeof(BSlot) * L.nslots) != cudaSuccess) return SVDSC_ERR_NOMEM;
+    cudaMemcpyAsync(L.d_slots, slots.data(), sizeof(BSlot) * L.nslots, cudaMemcpyHostToDevice, B->stream);
+    return cudaGetLastError() == cudaSuccess ? SVDSC_OK : SVDSC_ERR_CUDA;
 }
 
 int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const int *k, const int *p,
@@ -992,6 +1084,7 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     if (opt && opt->precision != SVDSC_MIXED) return SVDSC_ERR_ARG;  // the batched form is the mixed one
     if (opt && opt->which != SVDSC_LARGEST) return SVDSC_ERR_ARG;    // and keeps the largest triplets
     if (opt && opt->reorth != SVDSC_REORTH_FULL) return SVDSC_ERR_ARG;  // with full re-orthogonalization
+    if (opt && opt->block > 1) return SVDSC_ERR_ARG;                  // one vector at a time
     for (int b = 0; b < nb; b++) {
         const svdsc_matrix &a = As[b];
         if (a.format != SVDSC_CSR || a.m < 1 || a.n < 1) return SVDSC_ERR_ARG;
@@ -999,6 +1092,8 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
         const int t = pb < 0 ? std::max(15, 3 * k[b]) : k[b] + pb;
         if (k[b] < 1 || k[b] > kBMaxK || t < k[b] || t > kBMaxT || t > a.m || t + 1 > a.n) return SVDSC_ERR_SIZE;
     }
+    const int Cfix = opt ? opt->batch_cluster : 0;
+    if (Cfix != 0 && Cfix != 1 && Cfix != 2 && Cfix != 4 && Cfix != 8) return SVDSC_ERR_ARG;
     svdsc_batch *B = new (std::nothrow) svdsc_batch();
     if (!B) return SVDSC_ERR_NOMEM;
     B->nb = nb;
@@ -1010,7 +1105,9 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
         svdsc_batch_destroy(B);
         return SVDSC_ERR_CUDA;
     }
-    if (cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmBytes) !=
+    if (cudaFuncSetAttribute(tune_spmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float) * kXCap)) != cudaSuccess ||
+        cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmBytes) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel, kBT, kSmBytes) != cudaSuccess || occ < 1) {
         svdsc_batch_destroy(B);
@@ -1038,85 +1135,45 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
         tmax = std::max(tmax, M.t);
     }
     if (rc) { svdsc_batch_destroy(B); return rc; }
-    // cluster size: the smallest power of two (<= 8) for which the costliest
-    // matrix on its cluster takes at most its share of the batch's estimated
-    // work (restart counts are not known in advance and vary widely, so the
-    // rule leans towards larger clusters)
+    B->tstride = ((int64_t)(tmax + 1) * (tmax + 1) + 31) & ~int64_t(31);
+    // Estimated work of one Lanczos pass (restart counts are not known in
+    // advance): CGS2 ~ (m + n) t^2, products ~ nnz t.  The queue holds the
+    // matrices largest first.
     auto est_cost = [&](int b) {
         const BMat &M = B->hm[b];
         return (double)(M.m + M.n) * M.t * M.t + 4.0 * (double)M.nnz * M.t;
     };
-    double total = 0.0, worst = 0.0;
-    for (int b = 0; b < nb; b++) { total += est_cost(b); worst = std::max(worst, est_cost(b)); }
-    int C = 1;
-    while (C < 8 && worst * nsm > total * C) C *= 2;
-    if (opt && opt->batch_cluster > 0) C = opt->batch_cluster;  // explicit: 1, 2, 4 or 8
-    if (C != 1 && C != 2 && C != 4 && C != 8) { svdsc_batch_destroy(B); return SVDSC_ERR_ARG; }
-    B->csize = C;
-    {
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = C;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(C * 64);
-        cfg.blockDim = dim3(kBT);
-        cfg.dynamicSmemBytes = kSmBytes;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int ncl = 0;
-        if (cudaOccupancyMaxActiveClusters(&ncl, batched_kernel, &cfg) != cudaSuccess || ncl < 1) {
-            svdsc_batch_destroy(B);
-            return SVDSC_ERR_CUDA;
-        }
-        B->nslots = std::min(nb, ncl);  // clusters in the persistent grid
-    }
-    const int64_t ldu = (mmax + 63) & ~int64_t(63), ldv = (nmax + 63) & ~int64_t(63);
-    const int64_t cols = tmax + 2;
-    const size_t per_slot = sizeof(double) * (size_t)(2 * ldu * cols + 2 * ldv * cols + 64) +
-                            sizeof(float) * (size_t)(2 * ldu * cols + 2 * ldv * cols + std::max(ldu, ldv)) + 4096;
-    std::vector<BSlot> slots(B->nslots);
-    if (cudaMalloc(&B->slot_mem, per_slot * B->nslots) != cudaSuccess) { svdsc_batch_destroy(B); return SVDSC_ERR_NOMEM; }
-    cudaMemsetAsync(B->slot_mem, 0, per_slot * B->nslots, B->stream);
-    B->tstride = ((int64_t)(tmax + 1) * (tmax + 1) + 31) & ~int64_t(31);
-    if (cudaMalloc(&B->d_T, sizeof(double) * B->tstride * B->nslots * C) != cudaSuccess) {
-        svdsc_batch_destroy(B);
-        return SVDSC_ERR_NOMEM;
-    }
-    for (int s = 0; s < B->nslots; s++) {
-        uint8_t *base = (uint8_t *)B->slot_mem + per_slot * s;
-        auto take = [&](size_t bytes) { uint8_t *p = base; base += (bytes + 255) & ~(size_t)255; return p; };
-        BSlot &S = slots[s];
-        S.ldu = ldu; S.ldv = ldv;
-        S.U0 = (double *)take(sizeof(double) * ldu * cols);
-        S.U1 = (double *)take(sizeof(double) * ldu * cols);
-        S.V0 = (double *)take(sizeof(double) * ldv * cols);
-        S.V1 = (double *)take(sizeof(double) * ldv * cols);
-        S.U32_0 = (float *)take(sizeof(float) * ldu * cols);
-        S.U32_1 = (float *)take(sizeof(float) * ldu * cols);
-        S.V32_0 = (float *)take(sizeof(float) * ldv * cols);
-        S.V32_1 = (float *)take(sizeof(float) * ldv * cols);
-        S.wf = (float *)take(sizeof(float) * std::max(ldu, ldv));
-    }
-    // work order: largest estimated cost first
     std::vector<int> order(nb);
     for (int b = 0; b < nb; b++) order[b] = b;
-    std::sort(order.begin(), order.end(), [&](int x, int y) {
-        auto cost = [&](int b) { const BMat &M = B->hm[b]; return (double)(M.m + M.n) * M.t * M.t + (double)M.nnz * M.t * 4; };
-        return cost(x) > cost(y);
-    });
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return est_cost(x) > est_cost(y); });
+    double total = 0.0, worst = 0.0;
+    for (int b = 0; b < nb; b++) { total += est_cost(b); worst = std::max(worst, est_cost(b)); }
+    // Cluster size: the smallest power of two <= 8 for which the costliest
+    // matrix on its cluster stays within its share of the batch's estimated
+    // work.  (Two concurrent launches on one queue, 8-CTA clusters taking the
+    // largest matrices and 2-CTA clusters the smallest, measured slower: the
+    // matrix that dominates the batch is not among the largest by this
+    // estimate, because its cost is its restart count, unknown in advance.)
+    int C = Cfix;
+    if (C == 0) {
+        C = 1;
+        while (C < 8 && worst * nsm > total * C) C *= 2;
+    }
+    const int cap = max_clusters(C);
+    if (cap < 1) { svdsc_batch_destroy(B); return SVDSC_ERR_CUDA; }
+    B->L.csize = C;
+    B->L.nslots = std::min(nb, cap);
+    rc = setup_launch(B, B->L, mmax, nmax, tmax);
+    if (rc) { svdsc_batch_destroy(B); return rc; }
     bool ok = cudaMalloc(&B->d_mats, sizeof(BMat) * nb) == cudaSuccess &&
               cudaMalloc(&B->d_order, sizeof(int) * nb) == cudaSuccess &&
               cudaMalloc(&B->d_stats, sizeof(BStat) * nb) == cudaSuccess &&
-              cudaMalloc(&B->d_slots, sizeof(BSlot) * B->nslots) == cudaSuccess &&
               cudaMalloc(&B->d_prm, sizeof(BParams)) == cudaSuccess &&
-              cudaMalloc(&B->d_queue, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&B->d_next, sizeof(int)) == cudaSuccess &&
               cudaMallocHost(&B->h_mats, sizeof(BMat) * nb) == cudaSuccess &&
               cudaMallocHost(&B->h_prm, sizeof(BParams)) == cudaSuccess;
     if (!ok) { svdsc_batch_destroy(B); return SVDSC_ERR_NOMEM; }
     cudaMemcpyAsync(B->d_order, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, B->stream);
-    cudaMemcpyAsync(B->d_slots, slots.data(), sizeof(BSlot) * B->nslots, cudaMemcpyHostToDevice, B->stream);
     // device output staging (used when outputs go to the host)
     size_t tot = 0;
     B->out_off.resize(nb);
@@ -1152,6 +1209,26 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     return SVDSC_OK;
 }
 
+static cudaError_t launch_batched(svdsc_batch *B, cudaStream_t s)
+{
+    BLaunch &L = B->L;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = L.csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(L.nslots * L.csize);
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = kSmBytes;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batched_kernel, (const BMat *)B->d_mats, (const int *)B->d_order, B->nb,
+                              B->d_next, B->d_stats, (const BSlot *)L.d_slots, L.d_T, B->tstride,
+                              (const BParams *)B->d_prm);
+}
+
 int svdsc_batch_solve(svdsc_batch *B, double tol, int maxit, double *const *S, double *const *U,
                       double *const *V, double *const *res, int out_on_device, svdsc_info *infos)
 {
@@ -1171,27 +1248,22 @@ int svdsc_batch_solve(svdsc_batch *B, double tol, int maxit, double *const *S, d
     memcpy(B->h_mats, B->hm.data(), sizeof(BMat) * nb);
     B->h_prm->tol = tol;
     B->h_prm->maxit = maxit;
-    B->h_prm->nb = nb;
-    if (!B->exec) {  // capture upload + reset + persistent launch once; replay afterwards
+    B->h_prm->pad = 0;
+    if (!B->exec) {  // capture upload + reset + the persistent launch(es) once; replay afterwards
         if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SVDSC_ERR_CUDA;
         cudaMemcpyAsync(B->d_mats, B->h_mats, sizeof(BMat) * nb, cudaMemcpyHostToDevice, B->stream);
         cudaMemcpyAsync(B->d_prm, B->h_prm, sizeof(BParams), cudaMemcpyHostToDevice, B->stream);
-        cudaMemsetAsync(B->d_queue, 0, sizeof(int), B->stream);
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = B->csize;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(B->nslots * B->csize);
-        cfg.blockDim = dim3(kBT);
-        cfg.dynamicSmemBytes = kSmBytes;
-        cfg.stream = B->stream;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, batched_kernel, (const BMat *)B->d_mats, (const int *)B->d_order, B->d_stats,
-                           (const BSlot *)B->d_slots, B->d_T, B->tstride, (const BParams *)B->d_prm, B->d_queue);
-        if (cudaStreamEndCapture(B->stream, &B->graph) != cudaSuccess) return SVDSC_ERR_CUDA;
+        cudaMemsetAsync(B->d_next, 0, sizeof(int), B->stream);
+        cudaMemsetAsync(B->d_stats, 0, sizeof(BStat) * nb, B->stream);
+        const cudaError_t e = launch_batched(B, B->stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(B->stream, &g);
+        if (e != cudaSuccess || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return SVDSC_ERR_CUDA;
+        }
+        B->graph = g;
         if (cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess) return SVDSC_ERR_CUDA;
     }
     if (cudaGraphLaunch(B->exec, B->stream) != cudaSuccess) return SVDSC_ERR_CUDA;
@@ -1276,8 +1348,8 @@ int svdsc_batch_phase_cycles(const svdsc_batch *B, int64_t *cycles)
 int svdsc_batch_layout(const svdsc_batch *B, int *cluster_size, int *clusters)
 {
     if (!B) return SVDSC_ERR_ARG;
-    if (cluster_size) *cluster_size = B->csize;
-    if (clusters) *clusters = B->nslots;
+    if (cluster_size) *cluster_size = B->L.csize;
+    if (clusters) *clusters = B->L.nslots;
     return SVDSC_OK;
 }
 
