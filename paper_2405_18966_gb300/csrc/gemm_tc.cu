@@ -583,6 +583,219 @@ tc_gemm_kernel(const WT *__restrict__ W, int64_t ldw, int64_t rows, int t, int k
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---------------------------------------------------- row-tile form (FP64)
+// For 64 < k <= 128 the kernel above cuts every row of W once per 64-column
+// block of C, i.e. twice.  Here the roles of the operands are swapped so that
+// each W entry is cut once: the MMA's M dimension (128) holds all k output
+// columns (A operand = the digit slices of Q^T, prepared once and copied per
+// chunk), its N dimension 64 rows of W (B operand = the CTA's own cut of W).
+// The eight TMEM accumulators (one per digit weight g = s + s') of 64 columns
+// each fill the 512 columns; TMEM lane j holds output column j, TMEM column
+// n row n of the tile.  The arithmetic (digits, exact sums, recombination,
+// one rounding) is the same as above.
+constexpr int kRN = 64;                         // rows of W per CTA (MMA N)
+constexpr int kRCut = 512;                      // cutter threads: eight per row
+constexpr int kRThreads = kRCut + 32;           // + the MMA warp
+constexpr int kRTPR = kRCut / kRN;              // threads per row (8)
+constexpr int kREPT = kKC / kRTPR;              // W entries each cutter cuts per chunk (4)
+static_assert(kREPT == 4, "row-tile chunk split");
+constexpr int kRA_slice = 128 * kKC * 2;        // Q^T slice: 128 x 32 BF16 = 8 KB
+constexpr int kRB_slice = kRN * kKC * 2;        // W slice: 64 x 32 BF16 = 4 KB
+constexpr int kRStage = kDigits * (kRA_slice + kRB_slice);   // 96 KB
+constexpr int kRSmem = 2 * kRStage + 1024;
+
+__global__ void __launch_bounds__(kRThreads, 1)
+tc_gemm_rows_kernel(const double *__restrict__ W, int64_t ldw, int64_t rows, int t, int k,
+                    const uint16_t *__restrict__ Bs, const int *__restrict__ fexp, int nchunks,
+                    double *__restrict__ C, int64_t ldc, int *err)
+{
+    constexpr int S = kDigits;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t a_full[2], b_full[2], mma_done[2];
+    __shared__ uint32_t tmem_base_slot;
+    __shared__ int s_er[kRN];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool cutter = tid < kRCut;
+    const int trow = tid & (kRN - 1), part = tid >> 6;  // cutters: part in [0, 8)
+    const int64_t row0 = (int64_t)blockIdx.x * kRN;
+    const int64_t r = row0 + trow;
+    const bool row_ok = cutter && r < rows;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&a_full[i], kRCut / 32);
+            mbar_init(&b_full[i], 1);
+            mbar_init(&mma_done[i], 1);
+        }
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_slot;
+
+    // row exponents: each part scans every kRTPR-th column of its row
+    {
+        int e_h = -100000;
+        if (row_ok)
+            for (int c = part; c < t; c += kRTPR) e_h = max(e_h, dexp_of(W[r + (int64_t)c * ldw]));
+        if (cutter && part == 0) s_er[trow] = -100000;
+        __syncthreads();
+        if (cutter) atomicMax(&s_er[trow], e_h);
+        __syncthreads();
+    }
+    const int e_r = cutter ? s_er[trow] : 0;
+
+    uint32_t parity[2] = {0u, 0u};
+    bool used[2] = {false, false};
+    bool ok = true;
+    if (!cutter) {
+        // MMA warp, one thread: stage free -> bulk copy of the Q^T slices ->
+        // W slices cut and Q^T landed -> 36 products per 16-wide K step -> commit
+        if (lane == 0) {
+            uint32_t apar[2] = {0u, 0u}, bpar[2] = {0u, 0u};
+            for (int chunk = 0; chunk < nchunks; chunk++) {
+                const int st = chunk & 1;
+                uint8_t *Aq = smem + st * kRStage;               // Q^T slices (A operand)
+                uint8_t *Bw = Aq + S * kRA_slice;                // W slices (B operand)
+                if (used[st]) {
+                    if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
+                    parity[st] ^= 1u;
+                }
+                mbar_expect_tx(&b_full[st], (uint32_t)(S * kRA_slice));
+                bulk_g2s(Aq, Bs + (int64_t)chunk * S * (128 * kKC), (uint32_t)(S * kRA_slice), &b_full[st]);
+                if (!mbar_wait_bounded(&a_full[st], apar[st])) ok = false;
+                apar[st] ^= 1u;
+                if (!mbar_wait_bounded(&b_full[st], bpar[st])) ok = false;
+                bpar[st] ^= 1u;
+                tc_fence_after();
+                if (ok) {
+                    constexpr uint32_t idesc = idesc_bf16(128, kRN);
+                    const uint32_t a0 = smem_u32(Aq), b0 = smem_u32(Bw);
+                    constexpr uint32_t a_lbo = (128 / 8) * 128, a_sbo = 128;
+                    constexpr uint32_t b_lbo = (kRN / 8) * 128, b_sbo = 128;
+#pragma unroll
+                    for (int ks = 0; ks < kKC / 16; ks++) {
+#pragma unroll
+                        for (int s = 0; s < S; s++) {
+#pragma unroll
+                            for (int s2 = 0; s2 < S; s2++) {
+                                if (s + s2 > S - 1) continue;
+                                const int g = s + s2;
+                                const uint64_t ad = smem_desc(a0 + s * kRA_slice + ks * 2 * a_lbo, a_lbo, a_sbo);
+                                const uint64_t bd = smem_desc(b0 + s2 * kRB_slice + ks * 2 * b_lbo, b_lbo, b_sbo);
+                                // the first product into each accumulator overwrites it
+                                const bool first = chunk == 0 && ks == 0 && s == 0;
+                                umma_bf16(tmem + (uint32_t)(g * kRN), ad, bd, idesc, first ? 0u : 1u);
+                            }
+                        }
+                    }
+                }
+                umma_commit(&mma_done[st]);
+                used[st] = true;
+            }
+        }
+        __syncwarp();
+    } else {
+        // cutters: thread (row, part) cuts entries kk = 4 part .. 4 part + 3 of
+        // each chunk of its row; the next chunk's entries load while this one is cut
+        double cur[kREPT], nxt[kREPT];
+        auto load_chunk = [&](int chunk, double (&dst)[kREPT]) {
+#pragma unroll
+            for (int q = 0; q < kREPT; q++) {
+                const int c = chunk * kKC + part * kREPT + q;
+                dst[q] = (row_ok && c < t) ? W[r + (int64_t)c * ldw] : 0.0;
+            }
+        };
+        load_chunk(0, cur);
+        for (int chunk = 0; chunk < nchunks; chunk++) {
+            if (chunk + 1 < nchunks) load_chunk(chunk + 1, nxt);
+            const int st = chunk & 1;
+            uint8_t *Bw = smem + st * kRStage + S * kRA_slice;
+            if (used[st]) {
+                if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
+                parity[st] ^= 1u;
+            }
+            tc_fence_after();
+            uint32_t pc[kREPT][kDigits];
+#pragma unroll
+            for (int q = 0; q < kREPT; q++) ozaki_digits(cur[q], e_r, pc[q]);
+            // four BF16 values (high halves of the FP32 patterns) = 8 bytes per slice
+            const int off = core_off(trow, part * kREPT, kRN);
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                uint2 w2;
+                w2.x = __byte_perm(pc[0][s], pc[1][s], 0x7632);
+                w2.y = __byte_perm(pc[2][s], pc[3][s], 0x7632);
+                *(uint2 *)(Bw + s * kRB_slice + off) = w2;
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[st]);
+            used[st] = true;
+#pragma unroll
+            for (int q = 0; q < kREPT; q++) cur[q] = nxt[q];
+        }
+        for (int st = 0; st < 2; st++)
+            if (used[st]) {
+                if (!mbar_wait_bounded(&mma_done[st], parity[st])) ok = false;
+                parity[st] ^= 1u;
+            }
+    }
+    tc_fence_after();
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else if (cutter) {
+        // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. (output columns j);
+        // the four warp groups w / 4 take interleaved groups of 8 TMEM columns
+        // (rows of the tile).  Each thread then writes 8 consecutive rows of
+        // its column j of C.
+        const int jq = warp & 3, grp = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(jq * 32) << 16;
+        const int j = jq * 32 + lane;
+        const int ef = (j < k) ? fexp[j] : -100000;
+        for (int c8 = grp * 8; c8 < kRN; c8 += 32) {
+            if (row0 + c8 >= rows) break;  // uniform across the warp
+            long long zh[8], zl[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) { zh[q] = 0; zl[q] = 0; }
+#pragma unroll
+            for (int g = 0; g < kDigits; g++) {
+                uint32_t x[8];
+                tmem_ld8(tmem + lane_base + (uint32_t)(g * kRN + c8), x);
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const long long xi = (long long)__float2int_rn(__uint_as_float(x[q]));
+                    if (g < 4) zh[q] = zh[q] * 128 + xi;
+                    else zl[q] = zl[q] * 128 + xi;
+                }
+            }
+            if (j < k) {
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int64_t rr = row0 + c8 + q;
+                    if (rr >= rows) break;
+                    const int er = s_er[c8 + q];
+                    double o = 0.0;
+                    if (er > -99999 && ef > -99999 && !compose_f64(zh[q], zl[q], er + ef, o))
+                        o = ldexp(fma((double)zh[q], 0x1p-31, (double)zl[q] * 0x1p-59), er + ef);
+                    C[rr + (int64_t)j * ldc] = o;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 // ------------------------------------------------------------- host side
 
 template <int S, int NT, bool OZAKI>
@@ -653,6 +866,18 @@ cudaError_t tc_gemm(int mode, const double *W, const float *W32, int64_t ldw, in
     uint16_t *bs = (uint16_t *)ws;
     int *fx = (int *)((uint8_t *)ws + slices_bytes(t, k));
     if (launches) *launches += 2;
+    if (mode == 0 && k > 64 && k <= 128 && !C32) {
+        // every W entry cut once: the row-tile form (Q^T slices for 128 columns)
+        static std::atomic<unsigned long long> attr_done{0};
+        cudaError_t e = set_smem_limit_once((const void *)tc_gemm_rows_kernel, kRSmem, &attr_done);
+        if (e != cudaSuccess) return e;
+        const int nchunks = (t + kKC - 1) / kKC;
+        dim3 pg((unsigned)((128 + 127) / 128), (unsigned)nchunks);
+        prep_b_kernel<kDigits, 128, true><<<pg, 128, 0, s>>>(Q, ldq, t, k, nchunks, 1, bs, fx);
+        tc_gemm_rows_kernel<<<(unsigned)((rows + kRN - 1) / kRN), kRThreads, kRSmem, s>>>(
+            W, ldw, rows, t, k, bs, fx, nchunks, C, ldc, err);
+        return cudaGetLastError();
+    }
     if (mode == 0)
         return launch_tc<kDigits, 64, true, double>(W, ldw, rows, t, Q, ldq, k, C, ldc, C32, bs, fx, err, s);
     if (W32) return launch_tc<3, 128, false, float>(W32, ldw, rows, t, Q, ldq, k, C, ldc, C32, bs, fx, err, s);

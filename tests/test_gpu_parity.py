@@ -339,7 +339,9 @@ def test_mixed_precision_k100_vs_fp64_oracle(pkg, orc):
 # ------------------------------------------------- tensor-core restart GEMM
 
 @pytest.mark.parametrize("rows,t,k", [(1, 1, 1), (127, 16, 10), (128, 20, 10), (1000, 33, 49),
-                                      (50_001, 200, 100), (3000, 448, 48), (4096, 64, 64)])
+                                      (50_001, 200, 100), (3000, 448, 48), (4096, 64, 64),
+                                      # 64 < k <= 128: the row-tile form (each W entry cut once)
+                                      (1000, 80, 65), (65, 128, 128), (129, 448, 128), (63, 100, 97)])
 def test_tc_gemm_fp64_digits_vs_oracle(pkg, orc, torch_mod, rows, t, k):
     """Mode 0 (Ozaki-style digits on BF16 tcgen05 MMAs) against the oracle's FP64
     loop: error within 8 eps sum_c |W_rc| |Q_cj| (an FP64 GEMM's bound) plus
