@@ -512,30 +512,28 @@ def batch_bytes(info, m, n, nnz, k):
     return tot + info["restarts"] * per_restart
 
 
-def run_batch(args, ws, rank):
-    import torch
-    import paper_2405_18966_gb300 as pkg
-    from paper_2405_18966_gb300 import build as _build
-    _build.build()
+def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, plain_sample=8):
+    """Times the batched form on the synthetic batch (device outputs, the
+    graph replayed), with the per-cluster balance, the hand-off and the plain
+    FP64 form on a sample.  Returns (result dict, items, last outputs, batch)."""
     import synth
-    count = max(1, int(round(256 * args.batch_frac)))
     t0 = time.perf_counter()
-    items = synth.workload_batch(count=count, size_scale=args.scale)
+    items = synth.workload_batch(count=count, size_scale=scale)
     gen_s = time.perf_counter() - t0
     mats = [it.a for it in items]
     ks = [it.k for it in items]
     t0 = time.perf_counter()
-    b = pkg.Batch(mats, ks, ks, seed=1, cluster=args.batch_cluster)
+    b = pkg.Batch(mats, ks, ks, seed=1, cluster=cluster, handoff=handoff)
     create_s = time.perf_counter() - t0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         out = b.solve(1e-10, 1000, out="device")
     torch.cuda.synchronize()
     sampler = ClockSampler(None)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         out = b.solve(1e-10, 1000, out="device")
     torch.cuda.synchronize()
-    wall = (time.perf_counter() - t0) / args.steps
+    wall = (time.perf_counter() - t0) / steps
     clocks = sampler.stop()
     infos = out["infos"]
     nconv = sum(i["converged"] for i in infos)
@@ -546,7 +544,11 @@ def run_batch(args, ws, rank):
         per_cluster[int(c)] = per_cluster.get(int(c), 0) + int(cyc)
     loads = np.array(sorted(per_cluster.values())) / clk
     rs = np.array([i["restarts"] for i in infos])
+    lay = b.layout()
+    hand = b.handoff()
     balance = {"cluster_busy_s_max": float(loads.max()), "cluster_busy_s_mean": float(loads.mean()),
+               "note": "a handed-off matrix counts under its second-launch cluster with the cycles of both launches",
+               "ideal_s": float(prof["cycles_total"].sum() / clk / lay["clusters"]),
                "svd_share": float(prof["cycles_svd"].sum() / max(1, prof["cycles_total"].sum())),
                "phase_share": {nm: float(prof["cycles_phase"][:, q].sum() / max(1, prof["cycles_total"].sum()))
                                for q, nm in enumerate(("spmv", "cgs_fp32", "cgs_fp64", "norm_scale",
@@ -556,13 +558,13 @@ def run_batch(args, ws, rank):
                "slowest_matrix_s": float(prof["cycles_total"].max() / clk),
                "slowest": [{"m": int(items[i].a.m), "n": int(items[i].a.n), "nnz": int(items[i].a.nnz),
                             "k": int(items[i].k), "restarts": int(infos[i]["restarts"]),
-                            "s": float(prof["cycles_total"][i] / clk),
+                            "s": float(prof["cycles_total"][i] / clk), "handed_off": bool(prof["cluster"][i] >= 100000),
                             "svd_s": float(prof["cycles_svd"][i] / clk), "lbp_s": float(prof["cycles_lbp"][i] / clk)}
                            for i in np.argsort(-prof["cycles_total"])[:5]]}
+    balance["wall_over_ideal"] = wall / balance["ideal_s"]
     tot_bytes = sum(batch_bytes(inf, it.a.m, it.a.n, it.a.nnz, it.k) for inf, it in zip(infos, items))
-    launches = 1 * args.steps
     # plain GPU form (one svdsc_solve per matrix, FP64) on a sample, and the sigma error of the batch vs it
-    sample = list(range(0, count, max(1, count // 8)))[:8]
+    sample = list(range(0, count, max(1, count // plain_sample)))[:plain_sample]
     plain_s, errs = 0.0, []
     for i in sample:
         a64 = synth.CSR(items[i].a.m, items[i].a.n, items[i].a.row_ptr, items[i].a.col_idx,
@@ -577,6 +579,32 @@ def run_batch(args, ws, rank):
         Sb = out["S"][i].cpu().numpy()
         errs.append(float(np.max(np.abs(Sb - r.S) / r.S)))
     plain_est = plain_s / len(sample) * count
+    peaks, src = load_peaks()
+    gbs = tot_bytes / wall / 1e9
+    res = {"value": wall, "unit": "s", "steps": steps, "warmup": warmup, "clocks": clocks,
+           "gpu_launches": (2 if hand["idle_threshold"] > 0 else 1) * steps,
+           "config": {"workload": f"batch of {count} CSR matrices (m 2k-60k, n 1k-30k, 5-50 nnz/row, FP32, "
+                                  f"k 5-40, p = k), one persistent launch per solve (two with the hand-off)",
+                      "scale": scale, "matrices": count, "total_nnz": int(sum(a.nnz for a in mats)),
+                      "l2": "inputs larger than L2 (no flush)"},
+           "batch": {"converged": nconv, "restarts_mean": float(np.mean(rs)),
+                     "create_s": create_s, "generate_s": gen_s, "tuning": b.tuning(0), "layout": lay,
+                     "handoff": hand,
+                     "plain_fp64_gpu_s_estimate": plain_est, "speedup_vs_plain_gpu": plain_est / wall,
+                     "sigma_rel_err_vs_plain_fp64_max": max(errs), "plain_sample": len(sample),
+                     "balance": balance},
+           "hbm": {"alg_gbs": gbs, "frac_of_measured": gbs / peaks["hbm_gbs"]}}
+    return res, items, out, b
+
+
+def run_batch(args, ws, rank):
+    import torch
+    import paper_2405_18966_gb300 as pkg
+    from paper_2405_18966_gb300 import build as _build
+    _build.build()
+    count = max(1, int(round(256 * args.batch_frac)))
+    res, items, out, b = measure_batch(pkg, torch, count, args.scale, args.batch_cluster, args.batch_handoff,
+                                       args.warmup, args.steps)
     per_triplet = None
     if not args.no_per_triplet:
         idx = batch_sample_indices(count) if (count == 256 and args.scale == 1.0) else [0]
@@ -587,24 +615,13 @@ def run_batch(args, ws, rank):
                                                   [tonp(out["S"][i]) for i in idx],
                                                   [tonp(out["U"][i]) for i in idx],
                                                   [tonp(out["V"][i]) for i in idx])}
-    peaks, src = load_peaks()
-    gbs = tot_bytes / wall / 1e9
-    res = {"metric": METRIC, "value": wall, "unit": "s", "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-           "config": {"workload": f"batch of {count} CSR matrices (m 2k-60k, n 1k-30k, 5-50 nnz/row, FP32, "
-                                  f"k 5-40, p = k), one persistent launch per solve",
-                      "scale": args.scale, "matrices": count, "total_nnz": int(sum(a.nnz for a in mats)),
-                      "l2": "inputs larger than L2 (no flush)"},
-           "batch": {"converged": nconv, "restarts_mean": float(np.mean([i["restarts"] for i in infos])),
-                     "create_s": create_s, "generate_s": gen_s, "tuning": b.tuning(0), "layout": b.layout(),
-                     "plain_fp64_gpu_s_estimate": plain_est, "speedup_vs_plain_gpu": plain_est / wall,
-                     "sigma_rel_err_vs_plain_fp64_max": max(errs), "plain_sample": len(sample),
-                     "balance": balance},
-           "hbm": {"alg_gbs": gbs, "frac_of_measured": gbs / peaks["hbm_gbs"]},
-           "gpu_launches": launches, "clocks": clocks, "cpu_baseline": None, "e2e": None,
-           "per_triplet": per_triplet}
-    print(json.dumps(res), flush=True)
+    line = {"metric": METRIC, "value": res["value"], "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["value"] * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": res["config"], "batch": res["batch"], "hbm": res["hbm"],
+            "gpu_launches": res["gpu_launches"], "clocks": res["clocks"], "cpu_baseline": None, "e2e": None,
+            "per_triplet": per_triplet}
+    print(json.dumps(line), flush=True)
     b.close()
     return 0
 
@@ -685,6 +702,9 @@ def main():
     ap.add_argument("--no-per-triplet", action="store_true",
                     help="skip the per-triplet error report (mixed form on the 2,000 x 1,000 matrix and "
                          "a batch sample, against the FP64 oracle)")
+    ap.add_argument("--no-batch-form", action="store_true",
+                    help="skip the batched-form measurement of the default line (the 256-matrix batch, "
+                         "one warm-up and one timed solve)")
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--ref-restarts", type=int, default=None)
     ap.add_argument("--reorth", choices=["full", "partial"], default="full",
@@ -697,6 +717,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch-frac", type=float, default=1.0, help="fraction of the 256-matrix batch")
     ap.add_argument("--batch-cluster", type=int, default=0, help="CTAs per matrix (0: automatic)")
+    ap.add_argument("--batch-handoff", type=int, default=0,
+                    help="hand-off to 8-CTA clusters: 0 automatic, -1 never, h > 0 at h idle clusters")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
                     help="override the workload's precision (mixed: values rounded to FP32; the FP64 solve "
                          "of the same rounded matrix is run once, untimed, for the sigma error)")
@@ -903,6 +925,11 @@ def main():
     if rank == 0 and ws == 1 and not args.no_per_triplet:
         per_triplet = {"mixed_2000x1000_k100": per_triplet_mixed(pkg, torch),
                        "batch_sample": per_triplet_batch_minibatch(pkg)}
+    batch_form = None
+    if rank == 0 and ws == 1 and args.workload == "zipf" and args.scale == 1.0 and not args.no_batch_form:
+        bres, _, _, bb = measure_batch(pkg, torch, 256, 1.0, 0, 0, 1, 1)
+        bb.close()
+        batch_form = {k2: bres[k2] for k2 in ("value", "unit", "config", "batch", "hbm", "clocks")}
     vs_base, paper = None, None
     if args.workload in PAPER_S and args.scale == 1.0:
         # same size, spectrum, k, t, tol and round cap as the paper's DenseN; its
@@ -921,7 +948,7 @@ def main():
                      "phase_ms_per_step": phases_ms, "anorm_est": info["anorm_est"],
                      "sigma_1": float(r.S[0]), "sigma_k": float(r.S[k - 1])},
            "mixed_vs_fp64": mixed_vs_fp64, "per_triplet": per_triplet, "block_form": block_form,
-           "paper": paper}
+           "batch_form": batch_form, "paper": paper}
     if rank == 0:
         print(json.dumps(out), flush=True)
     solver.close()

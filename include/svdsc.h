@@ -127,6 +127,8 @@ typedef struct svdsc_options {
     int32_t which;         /* SVDSC_LARGEST (default) or SVDSC_SMALLEST */
     int32_t reorth;        /* SVDSC_REORTH_FULL (default) or SVDSC_REORTH_PARTIAL */
     int32_t block;         /* Lanczos block size: 0 or 1 (single vector, default), 2, 4, 8 or 16 */
+    int32_t batch_handoff; /* batched form, hand-off to a second launch: 0 automatic, -1 never,
+                              h > 0 once h clusters of the first launch are idle */
 } svdsc_options;
 
 /* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
@@ -320,9 +322,14 @@ int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, int64_t ldw,
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent truncated SVDs (uneven shapes and k) solved
- * in ONE persistent kernel launch, replayed from a CUDA graph.
- * Thread-block clusters (1-8 CTAs) take matrices from a work queue (largest
- * estimated cost first) and run Alg. 2 for each from start to finish.  Precision is the mixed form (FP32
+ * in one persistent kernel launch (two with the hand-off), replayed from a
+ * CUDA graph.  Thread-block clusters (1-8 CTAs) take matrices from a work
+ * queue (largest estimated cost first) and run Alg. 2 for each.  Hand-off:
+ * once the queue is empty and a set number of clusters are idle, the matrices
+ * still running stop at their next restart boundary (after the restart GEMM
+ * of Eq. 6) and a second launch of 8-CTA clusters resumes them from the saved
+ * state (U~_k, V~_k, v_{k+1}, sigma, rho, counters), so the last matrices run
+ * on more SMs than the first launch's cluster size gives them.  Precision is the mixed form (FP32
  * CSR values, FP32 SpMV and first CGS pass, FP64 second pass, norms, projected
  * SVD and residual test, FP32 restart GEMM); options.precision must be
  * SVDSC_MIXED.  Limits per matrix: CSR input, 1 <= k <= 48, t = k + p <= 80
@@ -359,6 +366,18 @@ int svdsc_batch_tuning(const svdsc_batch *b, int i, int *lanes_A, int *lanes_AT,
  * costliest matrix (estimated by the cost of one Lanczos pass), run on one
  * cluster, takes at most its share of the batch's estimated work. */
 int svdsc_batch_layout(const svdsc_batch *b, int *cluster_size, int *clusters);
+
+/* The hand-off set-up (each output may be NULL): the idle-cluster count that
+ * triggers it (0: no hand-off), the second launch's cluster size (8) and
+ * cluster count, and the number of matrices the last solve handed off (read
+ * from the device: call after svdsc_batch_solve has returned).  Automatic
+ * (options.batch_handoff = 0): on when the first launch's clusters are
+ * smaller than 8 CTAs and more numerous than the second launch's, with the
+ * threshold at which no more matrices are running than the second launch
+ * has clusters.  A handed-off matrix reports cluster 100000 + its cluster in
+ * the second launch in svdsc_batch_profile. */
+int svdsc_batch_handoff(const svdsc_batch *b, int *idle_threshold, int *cluster_size, int *clusters,
+                        int *handed_off);
 
 /* Per-matrix profile of the last batch solve (arrays of nb entries, each may
  * be NULL): SM clock cycles of the whole solve, of the projected SVDs and of

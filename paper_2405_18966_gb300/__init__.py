@@ -34,7 +34,7 @@ EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "sv
            "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc",
            "svdsc_gemm", "svdsc_batch_create", "svdsc_batch_solve", "svdsc_batch_tuning",
            "svdsc_batch_destroy", "svdsc_solve_batched", "svdsc_batch_layout", "svdsc_batch_profile",
-           "svdsc_batch_phase_cycles",
+           "svdsc_batch_phase_cycles", "svdsc_batch_handoff",
            "svdsc_selftest_wait")
 
 
@@ -49,7 +49,7 @@ class SvdscMatrix(C.Structure):
 class SvdscOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("timing", C.c_int32), ("seed", C.c_uint64),
                 ("restart_gemm", C.c_int32), ("batch_cluster", C.c_int32), ("which", C.c_int32),
-                ("reorth", C.c_int32), ("block", C.c_int32)]
+                ("reorth", C.c_int32), ("block", C.c_int32), ("batch_handoff", C.c_int32)]
 
 
 NUM_PHASES = 8
@@ -106,6 +106,7 @@ def lib():
         L.svdsc_batch_layout.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.svdsc_batch_profile.argtypes = [vp, vp, vp, vp, vp]
         L.svdsc_batch_phase_cycles.argtypes = [vp, vp]
+        L.svdsc_batch_handoff.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.svdsc_selftest_wait.argtypes = [vp, i32]
         L.svdsc_solve_batched.argtypes = [i32, C.POINTER(SvdscMatrix), vp, vp, dbl, i32, vp, vp, vp, vp,
                                           i32, C.POINTER(SvdscOptions), C.POINTER(SvdscInfo)]
@@ -326,16 +327,18 @@ def _csr_struct(A, keep):
 
 
 class Batch:
-    """Many truncated SVDs in one persistent launch (svdsc_batch_*), mixed precision."""
+    """Many truncated SVDs in one persistent launch (svdsc_batch_*), mixed precision.
+    handoff: 0 automatic, -1 never, h > 0 hand the running matrices to a second
+    launch of 8-CTA clusters once h clusters of the first are idle."""
 
-    def __init__(self, mats, k, p=None, seed: int = 0, cluster: int = 0):
+    def __init__(self, mats, k, p=None, seed: int = 0, cluster: int = 0, handoff: int = 0):
         keep = []
         nb = len(mats)
         arr = (SvdscMatrix * nb)(*[_csr_struct(a, keep) for a in mats])
         self.k = np.ascontiguousarray(k, dtype=np.int32)
         self.p = np.ascontiguousarray(p if p is not None else self.k, dtype=np.int32)
         self.shapes = [(int(a.m), int(a.n)) for a in mats]
-        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0, 0, 0)
+        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0, 0, 0, handoff)
         self.handle = C.c_void_p()
         _check(lib().svdsc_batch_create(C.byref(self.handle), nb, arr, _ptr(self.k), _ptr(self.p),
                                         C.byref(opt), None), "svdsc_batch_create")
@@ -344,6 +347,14 @@ class Batch:
         a, b = C.c_int(), C.c_int()
         _check(lib().svdsc_batch_layout(self.handle, C.byref(a), C.byref(b)), "svdsc_batch_layout")
         return {"cluster_size": a.value, "clusters": b.value}
+
+    def handoff(self):
+        """Hand-off set-up and the number of matrices handed off in the last solve."""
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().svdsc_batch_handoff(self.handle, C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
+               "svdsc_batch_handoff")
+        return {"idle_threshold": a.value, "cluster_size": b.value, "clusters": c.value,
+                "handed_off": d.value}
 
     def profile(self):
         nb = len(self.shapes)

@@ -44,6 +44,27 @@ struct BMat {
     double *S, *U, *V, *res;   // outputs (device), U: m x k (ld m), V: n x k (ld n)
     int gA, gAT, tc, pad;      // tuned: lanes per row for A and A^T, GEMV-T columns per warp
     uint64_t seed;
+    double *ckv;               // hand-off: v_{k+1} (n entries); U~_k and V~_k go to U and V
+    struct BHand *hand;        // hand-off: the rest of the restart state
+};
+
+// The state of a matrix handed from the first launch to the second at a
+// restart boundary, after the restart GEMM: U~_k (in the output U), V~_k (in
+// the output V), v_{k+1} (ckv), and this.
+struct BHand {
+    double anorm;
+    unsigned long long draws;
+    int restarts, it;
+    long long cycles_total, cycles_svd, cycles_lbp;
+    double S[kBMaxK], rho[kBMaxK];  // the k Ritz values and restart coefficients
+};
+
+// Queue state of one batch solve (device memory, reset by the graph).
+struct BQueue {
+    int next;      // next position in the first launch's queue
+    int idle;      // clusters of the first launch that found the queue empty
+    int ho_count;  // matrices handed to the second launch
+    int next2;     // next position in the hand-off list
 };
 
 struct BStat {
@@ -65,7 +86,8 @@ struct BSlot {   // one per cluster (bases), T one per CTA
 
 struct BParams {
     double tol;
-    int maxit, pad;
+    int maxit;
+    int handoff_idle;  // hand off once this many clusters are idle (0: never)
 };
 
 // ------------------------------------------------------------ cluster helpers
@@ -683,8 +705,65 @@ __device__ void cl_sign(BRun &R, double *U, int64_t ldU, double *V, int64_t ldV)
     }
 }
 
-__device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *Tpriv, const BParams &P,
-                          double *sm, float *smf, int &phase)
+// u_{k+1} = A v_{k+1} - U~ rho (Eq. 7), CGS2 against U~, alpha_{k+1}: the part
+// of the augmented restart after the restart GEMM and the new T.
+__device__ void restart_tail(BRun &R, const double *rho, double *red)
+{
+    const BMat &M = *R.M;
+    const int k = R.k;
+    double *uk = R.U + (int64_t)k * R.ldu;
+    cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32 + (int64_t)k * R.ldv, R.n, R.xs, R.m1 - R.m0, nullptr, 0.0,
+             uk + R.m0);
+    cta_update<double, double>(R.U + R.m0, R.ldu, k, rho, uk + R.m0, R.m1 - R.m0, false, red);
+    const double n2 = cl_cgs2(R, R.U, R.U32, R.ldu, k, uk, R.m0, R.m1);
+    const double ak = finish_vector(R, 0, k, n2);
+    if (threadIdx.x == 0) *Tb(R, k, k) = ak;
+    if (threadIdx.x == 0 && R.lead) { R.st->n_matvec++; R.st->n_steps++; }
+    __syncthreads();
+}
+
+// Hand-off copies of this CTA's rows between the cluster's bases (ld ldu,
+// ldv) and the matrix's global state (U~_k in MU, V~_k in MV, v_{k+1} in ckv;
+// leading dimensions m, n).  to_global: save, else load (with the FP32
+// shadows, the FP32 roundings of the FP64 values as the restart GEMM wrote
+// them).  Out of line: both run once per hand-off, and keeping them out of
+// the solver loop keeps its register allocation unchanged.
+__device__ __noinline__ void handoff_rows(bool to_global, double *MU, double *MV, double *ckv, int64_t m,
+                                          int64_t n, double *U, float *U32, int64_t ldu, double *V, float *V32,
+                                          int64_t ldv, int64_t m0, int64_t m1, int64_t n0, int64_t n1, int k)
+{
+    for (int j = 0; j <= k; j++) {
+        if (j < k)
+            for (int64_t r = m0 + threadIdx.x; r < m1; r += kBT) {
+                if (to_global) {
+                    MU[r + (int64_t)j * m] = U[r + (int64_t)j * ldu];
+                } else {
+                    const double x = MU[r + (int64_t)j * m];
+                    U[r + (int64_t)j * ldu] = x;
+                    U32[r + (int64_t)j * ldu] = (float)x;
+                }
+            }
+        double *src = j < k ? MV + (int64_t)j * n : ckv;  // column k: v_{k+1}
+        for (int64_t r = n0 + threadIdx.x; r < n1; r += kBT) {
+            if (to_global) {
+                src[r] = V[r + (int64_t)j * ldv];
+            } else {
+                const double x = src[r];
+                V[r + (int64_t)j * ldv] = x;
+                V32[r + (int64_t)j * ldv] = (float)x;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One matrix on this cluster.  mode 0: from the start; the matrix may be
+// handed off at a restart boundary (once P.handoff_idle clusters of this
+// launch found the queue empty), and is then finished by the second launch
+// (mode 1), which resumes from the saved state.  Returns nothing; the
+// outputs, or the hand-off state, are in global memory.
+__device__ void solve_one(const BMat &M, int b, BStat *st, const BSlot &slot, double *Tpriv, const BParams &P,
+                          double *sm, float *smf, int &phase, int mode, BQueue *q, int *ho_list)
 {
     BRun R;
     R.M = &M;
@@ -706,48 +785,72 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
     R.smf = smf;
     R.xs = (float *)(sm + kSmB);
     R.failed = false;
-    for (int q = 0; q < 5; q++) R.cyc[q] = 0;
+    for (int q2 = 0; q2 < 5; q2++) R.cyc[q2] = 0;
     double *red = sm + kSmRed;
     const int t = R.t, k = R.k;
     const long long c_start = clock64();
     long long c_svd = 0, c_lbp = 0;
-    if (threadIdx.x == 0 && R.lead) {
-        st->converged = 0; st->nconv = 0; st->restarts = 0; st->breakdowns = 0;
-        st->n_matvec = 0; st->n_steps = 0; st->err = 0; st->svd_sweeps = 0;
-        st->cluster = (int)cl_id();
-    }
-    for (int64_t i = threadIdx.x; i < (int64_t)(t + 1) * (t + 1); i += kBT) R.T[i] = 0.0;
-    // v_1: draw 0, normalised
-    for (int64_t j = R.n0 + threadIdx.x; j < R.n1; j += kBT) R.V[j] = normal_draw(R.key, 0, (uint64_t)j);
-    R.draws = 1;
-    __syncthreads();
-    {
-        const double nv = sqrt(cl_sum_scalar(R, cta_norm2(R.V + R.n0, R.n1 - R.n0, red)));
-        cta_scale(R.V + R.n0, R.V32 + R.n0, R.n1 - R.n0, 1.0 / nv);
-        cl_sync();
-    }
-    // u_1 = A v_1, alpha_1
-    cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32, R.n, R.xs, R.m1 - R.m0, nullptr, 0.0, R.U + R.m0);
-    {
-        const double a1 = finish_vector(R, 0, 0, cl_sum_scalar(R, cta_norm2(R.U + R.m0, R.m1 - R.m0, red)));
-        if (threadIdx.x == 0) *Tb(R, 0, 0) = a1;
-        if (threadIdx.x == 0 && R.lead) { st->n_matvec++; st->n_steps++; }
+    int restarts = 0, it0 = 1;
+    if (mode == 0) {
+        if (threadIdx.x == 0 && R.lead) {
+            st->converged = 0; st->nconv = 0; st->restarts = 0; st->breakdowns = 0;
+            st->n_matvec = 0; st->n_steps = 0; st->err = 0; st->svd_sweeps = 0;
+            st->cluster = (int)cl_id();
+            for (int q2 = 0; q2 < 5; q2++) st->cycles_phase[q2] = 0;
+        }
+        for (int64_t i = threadIdx.x; i < (int64_t)(t + 1) * (t + 1); i += kBT) R.T[i] = 0.0;
+        // v_1: draw 0, normalised
+        for (int64_t j = R.n0 + threadIdx.x; j < R.n1; j += kBT) R.V[j] = normal_draw(R.key, 0, (uint64_t)j);
+        R.draws = 1;
         __syncthreads();
-    }
-    {
+        {
+            const double nv = sqrt(cl_sum_scalar(R, cta_norm2(R.V + R.n0, R.n1 - R.n0, red)));
+            cta_scale(R.V + R.n0, R.V32 + R.n0, R.n1 - R.n0, 1.0 / nv);
+            cl_sync();
+        }
+        // u_1 = A v_1, alpha_1
+        cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32, R.n, R.xs, R.m1 - R.m0, nullptr, 0.0, R.U + R.m0);
+        {
+            const double a1 = finish_vector(R, 0, 0, cl_sum_scalar(R, cta_norm2(R.U + R.m0, R.m1 - R.m0, red)));
+            if (threadIdx.x == 0) *Tb(R, 0, 0) = a1;
+            if (threadIdx.x == 0 && R.lead) { st->n_matvec++; st->n_steps++; }
+            __syncthreads();
+        }
         const long long c0 = clock64();
         lbp_from(R, 1);
         c_lbp += clock64() - c0;
+    } else {
+        // resume: this CTA's rows of U~_k, V~_k and v_{k+1} (FP32 shadows are
+        // the FP32 roundings of the FP64 values, as the restart GEMM wrote
+        // them), T = [diag(sigma) rho], the restart coefficients, the counters
+        const BHand *H = M.hand;
+        handoff_rows(false, M.U, M.V, M.ckv, M.m, M.n, R.U, R.U32, R.ldu, R.V, R.V32, R.ldv, R.m0, R.m1, R.n0,
+                     R.n1, k);
+        for (int64_t i = threadIdx.x; i < (int64_t)(t + 1) * (t + 1); i += kBT) R.T[i] = 0.0;
+        __syncthreads();
+        if (threadIdx.x < k) {
+            const int j = threadIdx.x;
+            *Tb(R, j, j) = H->S[j];
+            *Tb(R, j, k) = H->rho[j];
+            sm[kSmRho + j] = H->rho[j];
+        }
+        R.anorm = H->anorm;
+        R.draws = H->draws;
+        restarts = H->restarts;
+        it0 = H->it;  // the first pass of the loop finishes that restart
+        if (threadIdx.x == 0 && R.lead) st->cluster = 100000 + (int)cl_id();
+        __syncthreads();
     }
-    int restarts = 0;
-    for (int it = 1; it <= P.maxit && !R.failed; it++) {
+    bool resume = mode == 1;
+    for (int it = it0; it <= P.maxit && !R.failed; it++) {
+        double *rho = sm + kSmRho;
+        if (!resume) {
         {
             const long long c0 = clock64();
             cta_small_svd(R);
             c_svd += clock64() - c0;
         }
         const double *S = sm + kSmS, *ut = sm + kSmUt;
-        double *rho = sm + kSmRho;
         const double beta_t = *Tb(R, t - 1, t);
         if (S[0] > R.anorm) R.anorm = S[0];
         int nconv = 0;
@@ -780,6 +883,39 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
             float *y = R.U32; R.U32 = R.U32a; R.U32a = y;
             y = R.V32; R.V32 = R.V32a; R.V32a = y;
         }
+        // hand-off test (first launch only): the decision of the cluster's first
+        // CTA, read by every CTA through the cluster reduction, so all agree
+        if (mode == 0 && P.handoff_idle > 0) {
+            double flag = 0.0;
+            if (threadIdx.x == 0 && R.lead)
+                flag = (*(volatile int *)&q->idle >= P.handoff_idle) ? 1.0 : 0.0;
+            if (cl_sum_scalar(R, flag) > 0.5) {
+                // save this CTA's rows of U~_k, V~_k, v_{k+1}; the first CTA the rest
+                handoff_rows(true, M.U, M.V, M.ckv, M.m, M.n, R.U, R.U32, R.ldu, R.V, R.V32, R.ldv, R.m0, R.m1,
+                             R.n0, R.n1, k);
+                if (R.lead) {
+                    BHand *H = M.hand;
+                    for (int j = threadIdx.x; j < k; j += kBT) {
+                        H->S[j] = S[j];
+                        H->rho[j] = rho[j];
+                    }
+                    if (threadIdx.x == 0) {
+                        H->anorm = R.anorm;
+                        H->draws = R.draws;
+                        H->restarts = restarts;
+                        H->it = it;
+                        H->cycles_total = clock64() - c_start;
+                        H->cycles_svd = c_svd;
+                        H->cycles_lbp = c_lbp;
+                        for (int q2 = 0; q2 < 5; q2++) st->cycles_phase[q2] = R.cyc[q2];
+                        ho_list[atomicAdd(&q->ho_count, 1)] = b;
+                    }
+                }
+                __syncthreads();
+                phase = R.phase;
+                return;
+            }
+        }
         for (int64_t i = threadIdx.x; i < (int64_t)(t + 1) * (t + 1); i += kBT) R.T[i] = 0.0;
         __syncthreads();
         if (threadIdx.x < k) {
@@ -788,17 +924,10 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
             *Tb(R, j, k) = rho[j];
         }
         __syncthreads();
+        }  // !resume
+        resume = false;
         cl_sync();  // v_{k+1} complete on every CTA before the product reads it
-        // u_{k+1} = A v_{k+1} - U~ rho (Eq. 7), CGS2 against U~
-        double *uk = R.U + (int64_t)k * R.ldu;
-        cta_spmv(M.gA, M.rp + R.m0, M.col, M.val, R.V32 + (int64_t)k * R.ldv, R.n, R.xs, R.m1 - R.m0, nullptr, 0.0,
-                 uk + R.m0);
-        cta_update<double, double>(R.U + R.m0, R.ldu, k, rho, uk + R.m0, R.m1 - R.m0, false, red);
-        const double n2 = cl_cgs2(R, R.U, R.U32, R.ldu, k, uk, R.m0, R.m1);
-        const double ak = finish_vector(R, 0, k, n2);
-        if (threadIdx.x == 0) *Tb(R, k, k) = ak;
-        if (threadIdx.x == 0 && R.lead) { st->n_matvec++; st->n_steps++; }
-        __syncthreads();
+        restart_tail(R, rho, red);
         restarts++;
         if (threadIdx.x == 0 && R.lead) st->restarts = restarts;
         const long long c0 = clock64();
@@ -817,19 +946,28 @@ __device__ void solve_one(const BMat &M, BStat *st, const BSlot &slot, double *T
         if (threadIdx.x == 0 && R.lead) st->anorm = R.anorm;
     }
     if (threadIdx.x == 0 && R.lead) {
-        st->cycles_total = clock64() - c_start;
+        long long c_tot = clock64() - c_start;
+        if (mode == 1) {  // add the first launch's share
+            c_tot += M.hand->cycles_total;
+            c_svd += M.hand->cycles_svd;
+            c_lbp += M.hand->cycles_lbp;
+        }
+        st->cycles_total = c_tot;
         st->cycles_svd = c_svd;
         st->cycles_lbp = c_lbp;
-        for (int q = 0; q < 5; q++) st->cycles_phase[q] = R.cyc[q];
+        for (int q2 = 0; q2 < 5; q2++) st->cycles_phase[q2] += R.cyc[q2];
     }
     phase = R.phase;
 }
 
-// The work queue: order[0..n) are matrix ids, largest estimated cost first;
-// *next is the next position to take.
+// The persistent kernel.  mode 0 takes matrices from the queue order[0..n),
+// largest estimated cost first; a cluster that finds it empty counts itself
+// idle and leaves.  mode 1 (the second launch, larger clusters) resumes the
+// matrices the first launch handed off.
 __global__ void __launch_bounds__(kBT, 1)
-batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, int n, int *next, BStat *stats,
-               const BSlot *__restrict__ slots, double *Tall, int64_t tstride, const BParams *prm)
+batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, int n, BQueue *q, int *ho_list,
+               int mode, BStat *stats, const BSlot *__restrict__ slots, double *Tall, int64_t tstride,
+               const BParams *prm)
 {
     extern __shared__ __align__(16) double bsm[];
     double *sm = bsm;
@@ -843,15 +981,23 @@ batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, int
         __syncthreads();
         cl_sync();  // every CTA has read the previous item
         if (threadIdx.x == 0 && cl_rank() == 0) {
-            const int i = atomicAdd(next, 1);
-            item = i < n ? order[i] : -1;
+            int b = -1;
+            if (mode == 0) {
+                const int i = atomicAdd(&q->next, 1);
+                if (i < n) b = order[i];
+                else atomicAdd(&q->idle, 1);
+            } else {
+                const int i = atomicAdd(&q->next2, 1);
+                if (i < *(volatile int *)&q->ho_count) b = ho_list[i];
+            }
+            item = b;
         }
         __syncthreads();
         cl_sync();
         const int b = cl_ld_i32(&item, 0);
         cl_sync();  // no CTA leaves while another still reads its shared memory
         if (b < 0) break;
-        solve_one(mats[b], stats + b, slot, Tpriv, P, sm, smf, phase);
+        solve_one(mats[b], b, stats + b, slot, Tpriv, P, sm, smf, phase, mode, q, ho_list);
     }
 }
 
@@ -889,6 +1035,9 @@ struct BLaunch {
     void *slot_mem = nullptr;
     BSlot *d_slots = nullptr;
     double *d_T = nullptr;
+    size_t slot_bytes = 0;       // bytes of slot_mem
+    int64_t t_count = 0;         // doubles of d_T
+    bool owns = true;            // false: slot_mem and d_T belong to another launch
 };
 
 struct svdsc_batch {
@@ -902,9 +1051,14 @@ struct svdsc_batch {
     BStat *d_stats = nullptr;
     BParams *d_prm = nullptr;
     int *d_order = nullptr;      // matrix ids, largest estimated cost first
-    int *d_next = nullptr;       // next queue position
+    BQueue *d_q = nullptr;       // queue positions and hand-off counters
     int64_t tstride = 0;
-    BLaunch L;
+    BLaunch L;                   // the first launch (all matrices)
+    BLaunch L2;                  // the second launch (matrices handed off), csize 0 when off
+    int handoff_idle = 0;        // hand off once this many clusters of L are idle (0: never)
+    int *d_ho = nullptr;         // hand-off list (nb entries)
+    double *ckv_mem = nullptr;   // v_{k+1} of each matrix (sum of n)
+    BHand *d_hand = nullptr;     // nb entries
     double *out_mem = nullptr;   // device outputs when the caller wants host outputs
     std::vector<size_t> out_off;
     cudaGraph_t graph = nullptr;
@@ -997,9 +1151,11 @@ extern "C" {
 
 static void free_launch(BLaunch &L)
 {
-    cudaFree(L.slot_mem);
+    if (L.owns) {
+        cudaFree(L.slot_mem);
+        cudaFree(L.d_T);
+    }
     cudaFree(L.d_slots);
-    cudaFree(L.d_T);
     L = BLaunch();
 }
 
@@ -1017,7 +1173,11 @@ int svdsc_batch_destroy(svdsc_batch *B)
     cudaFree(B->d_stats);
     cudaFree(B->d_prm);
     cudaFree(B->d_order);
-    cudaFree(B->d_next);
+    cudaFree(B->d_q);
+    cudaFree(B->d_ho);
+    cudaFree(B->ckv_mem);
+    cudaFree(B->d_hand);
+    free_launch(B->L2);  // may alias L's memory: freed first, without it
     free_launch(B->L);
     cudaFree(B->out_mem);
     if (B->stream) cudaStreamDestroy(B->stream);
@@ -1045,16 +1205,27 @@ static int max_clusters(int C)
 
 // Workspace of one launch: a slot (two sets of bases, FP64 and FP32) per
 // cluster, sized for the largest matrix, and a projected matrix per CTA.
-static int setup_launch(svdsc_batch *B, BLaunch &L, int64_t mmax, int64_t nmax, int tmax)
+// With `alias`, the memory of that launch is reused when it is large enough
+// (the two launches run one after the other on one stream).
+static int setup_launch(svdsc_batch *B, BLaunch &L, int64_t mmax, int64_t nmax, int tmax,
+                        const BLaunch *alias = nullptr)
 {
     const int64_t ldu = (mmax + 63) & ~int64_t(63), ldv = (nmax + 63) & ~int64_t(63);
     const int64_t cols = tmax + 2;
     const size_t per_slot = sizeof(double) * (size_t)(2 * ldu * cols + 2 * ldv * cols + 64) +
                             sizeof(float) * (size_t)(2 * ldu * cols + 2 * ldv * cols + std::max(ldu, ldv)) + 4096;
     std::vector<BSlot> slots(L.nslots);
-    if (cudaMalloc(&L.slot_mem, per_slot * L.nslots) != cudaSuccess) return SVDSC_ERR_NOMEM;
-    cudaMemsetAsync(L.slot_mem, 0, per_slot * L.nslots, B->stream);
-    if (cudaMalloc(&L.d_T, sizeof(double) * B->tstride * L.nslots * L.csize) != cudaSuccess) return SVDSC_ERR_NOMEM;
+    L.slot_bytes = per_slot * L.nslots;
+    L.t_count = B->tstride * L.nslots * L.csize;
+    if (alias && alias->slot_bytes >= L.slot_bytes && alias->t_count >= L.t_count) {
+        L.slot_mem = alias->slot_mem;
+        L.d_T = alias->d_T;
+        L.owns = false;
+    } else {
+        if (cudaMalloc(&L.slot_mem, L.slot_bytes) != cudaSuccess) return SVDSC_ERR_NOMEM;
+        cudaMemsetAsync(L.slot_mem, 0, L.slot_bytes, B->stream);
+        if (cudaMalloc(&L.d_T, sizeof(double) * L.t_count) != cudaSuccess) return SVDSC_ERR_NOMEM;
+    }
     for (int s = 0; s < L.nslots; s++) {
         uint8_t *base = (uint8_t *)L.slot_mem + per_slot * s;
         auto take = [&](size_t bytes) { uint8_t *p = base; base += (bytes + 255) & ~(size_t)255; return p; };
@@ -1094,6 +1265,8 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     }
     const int Cfix = opt ? opt->batch_cluster : 0;
     if (Cfix != 0 && Cfix != 1 && Cfix != 2 && Cfix != 4 && Cfix != 8) return SVDSC_ERR_ARG;
+    const int Hopt = opt ? opt->batch_handoff : 0;
+    if (Hopt < -1) return SVDSC_ERR_ARG;
     svdsc_batch *B = new (std::nothrow) svdsc_batch();
     if (!B) return SVDSC_ERR_NOMEM;
     B->nb = nb;
@@ -1165,14 +1338,47 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     B->L.nslots = std::min(nb, cap);
     rc = setup_launch(B, B->L, mmax, nmax, tmax);
     if (rc) { svdsc_batch_destroy(B); return rc; }
+    // Hand-off: once the queue is empty and enough clusters are idle, the
+    // matrices still running stop at their next restart boundary and a
+    // second launch of 8-CTA clusters finishes them.  Automatic: when the
+    // first launch has more clusters than the second can hold, from the
+    // moment no more are busy than the second launch has clusters.
+    if (C < 8 && Hopt >= 0) {
+        const int cap8 = max_clusters(8);
+        int thr = 0;
+        if (Hopt > 0) thr = Hopt;
+        else if (cap8 >= 1 && B->L.nslots > cap8) thr = B->L.nslots - cap8;
+        if (thr > 0 && cap8 >= 1) {
+            B->handoff_idle = thr;
+            B->L2.csize = 8;
+            B->L2.nslots = std::max(1, std::min(cap8, B->L.nslots - std::min(thr, B->L.nslots - 1)));
+            rc = setup_launch(B, B->L2, mmax, nmax, tmax, &B->L);
+            if (rc) { svdsc_batch_destroy(B); return rc; }
+        }
+    }
+    int64_t ntot = 0;
+    for (int b = 0; b < nb; b++) ntot += B->hm[b].n;
     bool ok = cudaMalloc(&B->d_mats, sizeof(BMat) * nb) == cudaSuccess &&
               cudaMalloc(&B->d_order, sizeof(int) * nb) == cudaSuccess &&
               cudaMalloc(&B->d_stats, sizeof(BStat) * nb) == cudaSuccess &&
               cudaMalloc(&B->d_prm, sizeof(BParams)) == cudaSuccess &&
-              cudaMalloc(&B->d_next, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&B->d_q, sizeof(BQueue)) == cudaSuccess &&
               cudaMallocHost(&B->h_mats, sizeof(BMat) * nb) == cudaSuccess &&
               cudaMallocHost(&B->h_prm, sizeof(BParams)) == cudaSuccess;
+    if (ok && B->handoff_idle > 0)
+        ok = cudaMalloc(&B->d_ho, sizeof(int) * nb) == cudaSuccess &&
+             cudaMalloc(&B->ckv_mem, sizeof(double) * ntot) == cudaSuccess &&
+             cudaMalloc(&B->d_hand, sizeof(BHand) * nb) == cudaSuccess;
     if (!ok) { svdsc_batch_destroy(B); return SVDSC_ERR_NOMEM; }
+    if (B->handoff_idle > 0) {
+        int64_t off = 0;
+        for (int b = 0; b < nb; b++) {
+            B->hm[b].ckv = B->ckv_mem + off;
+            B->hm[b].hand = B->d_hand + b;
+            off += B->hm[b].n;
+        }
+    }
+    cudaMemsetAsync(B->d_q, 0, sizeof(BQueue), B->stream);
     cudaMemcpyAsync(B->d_order, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, B->stream);
     // device output staging (used when outputs go to the host)
     size_t tot = 0;
@@ -1209,9 +1415,8 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     return SVDSC_OK;
 }
 
-static cudaError_t launch_batched(svdsc_batch *B, cudaStream_t s)
+static cudaError_t launch_batched(svdsc_batch *B, const BLaunch &L, int mode, cudaStream_t s)
 {
-    BLaunch &L = B->L;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1225,7 +1430,7 @@ static cudaError_t launch_batched(svdsc_batch *B, cudaStream_t s)
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, batched_kernel, (const BMat *)B->d_mats, (const int *)B->d_order, B->nb,
-                              B->d_next, B->d_stats, (const BSlot *)L.d_slots, L.d_T, B->tstride,
+                              B->d_q, B->d_ho, mode, B->d_stats, (const BSlot *)L.d_slots, L.d_T, B->tstride,
                               (const BParams *)B->d_prm);
 }
 
@@ -1248,14 +1453,15 @@ int svdsc_batch_solve(svdsc_batch *B, double tol, int maxit, double *const *S, d
     memcpy(B->h_mats, B->hm.data(), sizeof(BMat) * nb);
     B->h_prm->tol = tol;
     B->h_prm->maxit = maxit;
-    B->h_prm->pad = 0;
+    B->h_prm->handoff_idle = B->handoff_idle;
     if (!B->exec) {  // capture upload + reset + the persistent launch(es) once; replay afterwards
         if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SVDSC_ERR_CUDA;
         cudaMemcpyAsync(B->d_mats, B->h_mats, sizeof(BMat) * nb, cudaMemcpyHostToDevice, B->stream);
         cudaMemcpyAsync(B->d_prm, B->h_prm, sizeof(BParams), cudaMemcpyHostToDevice, B->stream);
-        cudaMemsetAsync(B->d_next, 0, sizeof(int), B->stream);
+        cudaMemsetAsync(B->d_q, 0, sizeof(BQueue), B->stream);
         cudaMemsetAsync(B->d_stats, 0, sizeof(BStat) * nb, B->stream);
-        const cudaError_t e = launch_batched(B, B->stream);
+        cudaError_t e = launch_batched(B, B->L, 0, B->stream);
+        if (e == cudaSuccess && B->handoff_idle > 0) e = launch_batched(B, B->L2, 1, B->stream);
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(B->stream, &g);
         if (e != cudaSuccess || ec != cudaSuccess) {
@@ -1350,6 +1556,21 @@ int svdsc_batch_layout(const svdsc_batch *B, int *cluster_size, int *clusters)
     if (!B) return SVDSC_ERR_ARG;
     if (cluster_size) *cluster_size = B->L.csize;
     if (clusters) *clusters = B->L.nslots;
+    return SVDSC_OK;
+}
+
+int svdsc_batch_handoff(const svdsc_batch *B, int *idle_threshold, int *cluster_size, int *clusters,
+                        int *handed_off)
+{
+    if (!B) return SVDSC_ERR_ARG;
+    if (idle_threshold) *idle_threshold = B->handoff_idle;
+    if (cluster_size) *cluster_size = B->L2.csize;
+    if (clusters) *clusters = B->L2.nslots;
+    if (handed_off) {
+        BQueue q = {};
+        if (cudaMemcpy(&q, B->d_q, sizeof(BQueue), cudaMemcpyDeviceToHost) != cudaSuccess) return SVDSC_ERR_CUDA;
+        *handed_off = q.ho_count;
+    }
     return SVDSC_OK;
 }
 

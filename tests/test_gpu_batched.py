@@ -96,6 +96,41 @@ def test_batched_uneven_shapes_vs_oracle(pkg, orc, cluster):
     b.close()
 
 
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_batched_handoff_vs_oracle(pkg, orc, cluster):
+    """Hand-off forced at the first idle cluster: the matrices still running
+    stop at a restart boundary and a second launch of 8-CTA clusters resumes
+    them.  Every result against the oracle as above; the counters carry over
+    (the product count of Eq. 8 still holds); solved twice from the graph."""
+    items = synth.workload_batch(count=10, size_scale=0.08, seed=7)
+    b = pkg.Batch([it.a for it in items], [it.k for it in items], [it.k for it in items], seed=3,
+                  cluster=cluster, handoff=1)
+    h = b.handoff()
+    assert h["idle_threshold"] == 1 and h["cluster_size"] == 8 and h["clusters"] >= 1
+    for rep in range(2):
+        out = b.solve(1e-10, 200)
+        h = b.handoff()
+        cl = b.profile()["cluster"]
+        assert h["handed_off"] >= 1, h
+        assert int(np.sum(cl >= 100000)) == h["handed_off"]
+        for i, it in enumerate(items):
+            info = out["infos"][i]
+            assert info["err"] == 0 and info["converged"] == 1, (i, info)
+            check_vs_oracle(orc, it.a, it.k, out["S"][i], out["U"][i], out["V"][i], maxit=200)
+            assert info["n_matvec"] == 2 * info["t"] + 2 * info["restarts"] * (info["t"] - it.k)
+    b.close()
+
+
+def test_batched_handoff_off(pkg):
+    items = synth.workload_batch(count=4, size_scale=0.05, seed=11)
+    b = pkg.Batch([it.a for it in items], [it.k for it in items], seed=5, cluster=1, handoff=-1)
+    assert b.handoff()["idle_threshold"] == 0 and b.handoff()["cluster_size"] == 0
+    out = b.solve(1e-10, 100)
+    assert b.handoff()["handed_off"] == 0
+    assert all(i["converged"] == 1 for i in out["infos"])
+    b.close()
+
+
 def test_batched_graph_replay_is_deterministic_and_device_outputs(pkg):
     items = synth.workload_batch(count=6, size_scale=0.05, seed=11)
     b = pkg.Batch([it.a for it in items], [it.k for it in items], seed=5)
