@@ -151,11 +151,14 @@ __device__ __forceinline__ int cl_ld_i32(const int *p, uint32_t rank)
 constexpr int kSmB = 0;                               // B: t x t (Jacobi columns)
 constexpr int kSmW = kSmB + kBMaxT * kBMaxT;          // W: t x t (rotations)
 // The sparse products gather from a copy of the whole input vector (FP32) in
-// shared memory when it fits in B and W, which only the projected SVD uses
-// (never during a product).  (A larger dedicated region was measured slower:
-// it shrinks the L1 cache that the gathers of longer vectors rely on.)
-constexpr int kXCap = 2 * (2 * kBMaxT * kBMaxT);      // 25,600 floats
-constexpr int kSmS = kSmW + kBMaxT * kBMaxT;          // sorted sigma (t)
+// shared memory when it fits in the region of B and W, which only the
+// projected SVD uses (never during a product); the region is padded to hold
+// 30,720 floats, every v-side vector of the batch workload (n <= 30,000).
+// (A much larger dedicated region was measured slower: it shrinks the L1
+// cache that the gathers of longer vectors rely on.)
+constexpr int kXCap = 30720;                          // floats
+constexpr int kSmBW = (kXCap / 2 > 2 * kBMaxT * kBMaxT) ? kXCap / 2 : 2 * kBMaxT * kBMaxT;
+constexpr int kSmS = kSmB + kSmBW;                    // sorted sigma (t)
 constexpr int kSmUt = kSmS + kBMaxT;                  // Uh(t, j) for j < k
 constexpr int kSmRho = kSmUt + kBMaxT;                // rho (k)
 constexpr int kSmH = kSmRho + kBMaxT;                 // projection coefficients (t + 2)
