@@ -146,7 +146,7 @@ def test_cgs2_vs_oracle_small_cta_layout(pkg, orc, torch_mod, ncols):
 
 # ---------------------------------------------------------- projected SVD
 
-@pytest.mark.parametrize("t", [1, 2, 20, 63, 64, 65, 128, 201])
+@pytest.mark.parametrize("t", [1, 2, 20, 63, 64, 65, 128, 201, 224, 225])
 def test_small_svd_vs_oracle(pkg, orc, torch_mod, t):
     torch = torch_mod
     rng = np.random.default_rng(t)
@@ -178,6 +178,28 @@ def test_small_svd_rank_deficient(pkg, orc, torch_mod):
     Uh = Uh.cpu().numpy()
     np.testing.assert_allclose(Uh.T @ Uh, np.eye(t), atol=1e-12)
     assert S.cpu().numpy()[-2:].max() < 1e-14
+
+
+@pytest.mark.parametrize("t,scale", [(150, 1.0), (200, 1e60), (200, 1e-60)])
+def test_small_svd_multi_cta_rank_deficient_and_scaled(pkg, orc, torch_mod, t, scale):
+    """The multi-CTA Jacobi (t > 64) with zero columns (rank deficiency) and
+    with entries far outside FP32's range, against the oracle's Jacobi."""
+    torch = torch_mod
+    rng = np.random.default_rng(t)
+    T = np.triu(rng.standard_normal((t, t))) * scale
+    T[:, 7] = 0.0
+    T[:, 90] = 0.0
+    _, s_ref, _, _ = orc.jacobi_svd(T)
+    A = synth.csr_uniform(2 * t + 2, 2 * t + 2, 0.01, 1)
+    with pkg.Solver(A) as s:
+        s.reserve(t)
+        S, Uh, Vh = s.small_svd(torch.tensor(T, device="cuda"))
+    S, Uh, Vh = S.cpu().numpy(), Uh.cpu().numpy(), Vh.cpu().numpy()
+    np.testing.assert_allclose(S, s_ref, rtol=1e-13, atol=1e-14 * s_ref[0])
+    assert S[-2:].max() < 1e-14 * s_ref[0]
+    np.testing.assert_allclose(Uh @ np.diag(S) @ Vh.T, T, atol=1e-13 * s_ref[0])
+    np.testing.assert_allclose(Vh.T @ Vh, np.eye(t), atol=1e-13)
+    np.testing.assert_allclose(Uh.T @ Uh, np.eye(t), atol=1e-12)
 
 
 # ------------------------------------------------------------ full solves
