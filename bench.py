@@ -512,7 +512,7 @@ def batch_bytes(info, m, n, nnz, k):
     return tot + info["restarts"] * per_restart
 
 
-def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, plain_sample=8):
+def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, plain_sample=8, order=0):
     """Times the batched form on the synthetic batch (device outputs, the
     graph replayed), with the per-cluster balance, the hand-off and the plain
     FP64 form on a sample.  Returns (result dict, items, last outputs, batch)."""
@@ -523,10 +523,16 @@ def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, pla
     mats = [it.a for it in items]
     ks = [it.k for it in items]
     t0 = time.perf_counter()
-    b = pkg.Batch(mats, ks, ks, seed=1, cluster=cluster, handoff=handoff)
+    b = pkg.Batch(mats, ks, ks, seed=1, cluster=cluster, handoff=handoff, order=order)
     create_s = time.perf_counter() - t0
-    for _ in range(warmup):
+    first_s = None
+    for w_i in range(warmup):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         out = b.solve(1e-10, 1000, out="device")
+        torch.cuda.synchronize()
+        if w_i == 0:
+            first_s = time.perf_counter() - t0  # queue ordered by the size estimate
     torch.cuda.synchronize()
     sampler = ClockSampler(None)
     t0 = time.perf_counter()
@@ -590,6 +596,9 @@ def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, pla
            "batch": {"converged": nconv, "restarts_mean": float(np.mean(rs)),
                      "create_s": create_s, "generate_s": gen_s, "tuning": b.tuning(0), "layout": lay,
                      "handoff": hand,
+                     "queue_order": "cycles each matrix took in the previous solve of the batch (largest "
+                                    "first); the first solve, by the size estimate, took first_solve_s",
+                     "first_solve_s": first_s,
                      "plain_fp64_gpu_s_estimate": plain_est, "speedup_vs_plain_gpu": plain_est / wall,
                      "sigma_rel_err_vs_plain_fp64_max": max(errs), "plain_sample": len(sample),
                      "balance": balance},
@@ -604,7 +613,7 @@ def run_batch(args, ws, rank):
     _build.build()
     count = max(1, int(round(256 * args.batch_frac)))
     res, items, out, b = measure_batch(pkg, torch, count, args.scale, args.batch_cluster, args.batch_handoff,
-                                       args.warmup, args.steps)
+                                       args.warmup, args.steps, order=args.batch_order)
     per_triplet = None
     if not args.no_per_triplet:
         idx = batch_sample_indices(count) if (count == 256 and args.scale == 1.0) else [0]
@@ -717,6 +726,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch-frac", type=float, default=1.0, help="fraction of the 256-matrix batch")
     ap.add_argument("--batch-cluster", type=int, default=0, help="CTAs per matrix (0: automatic)")
+    ap.add_argument("--batch-order", type=int, default=0,
+                    help="batch queue order: 0 the previous solve's measured cycles, 1 the size estimate")
     ap.add_argument("--batch-handoff", type=int, default=0,
                     help="hand-off to 8-CTA clusters: 0 automatic, -1 never, h > 0 at h idle clusters")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,

@@ -129,6 +129,9 @@ typedef struct svdsc_options {
     int32_t block;         /* Lanczos block size: 0 or 1 (single vector, default), 2, 4, 8 or 16 */
     int32_t batch_handoff; /* batched form, hand-off to a second launch: 0 automatic, -1 never,
                               h > 0 once h clusters of the first launch are idle */
+    int32_t batch_order;   /* batched form, queue order: 0 = estimated cost for the first solve, then
+                              the cycles each matrix took in the previous solve of the batch; 1 =
+                              the estimate always */
 } svdsc_options;
 
 /* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
@@ -324,7 +327,9 @@ int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, int64_t ldw,
  * Batched form: many independent truncated SVDs (uneven shapes and k) solved
  * in one persistent kernel launch (two with the hand-off), replayed from a
  * CUDA graph.  Thread-block clusters (1-8 CTAs) take matrices from a work
- * queue (largest estimated cost first) and run Alg. 2 for each.  Hand-off:
+ * queue (largest cost first: estimated from the sizes for the first solve,
+ * then, unless options.batch_order = 1, the cycles each matrix took in the
+ * previous solve of the same batch) and run Alg. 2 for each.  Hand-off:
  * once the queue is empty and a set number of clusters are idle, the matrices
  * still running stop at their next restart boundary (after the restart GEMM
  * of Eq. 6) and a second launch of 8-CTA clusters resumes them from the saved

@@ -49,7 +49,8 @@ class SvdscMatrix(C.Structure):
 class SvdscOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("timing", C.c_int32), ("seed", C.c_uint64),
                 ("restart_gemm", C.c_int32), ("batch_cluster", C.c_int32), ("which", C.c_int32),
-                ("reorth", C.c_int32), ("block", C.c_int32), ("batch_handoff", C.c_int32)]
+                ("reorth", C.c_int32), ("block", C.c_int32), ("batch_handoff", C.c_int32),
+                ("batch_order", C.c_int32)]
 
 
 NUM_PHASES = 8
@@ -329,16 +330,18 @@ def _csr_struct(A, keep):
 class Batch:
     """Many truncated SVDs in one persistent launch (svdsc_batch_*), mixed precision.
     handoff: 0 automatic, -1 never, h > 0 hand the running matrices to a second
-    launch of 8-CTA clusters once h clusters of the first are idle."""
+    launch of 8-CTA clusters once h clusters of the first are idle.
+    order: 0 queue by the previous solve's measured cycles (the size estimate
+    for the first solve), 1 by the estimate always."""
 
-    def __init__(self, mats, k, p=None, seed: int = 0, cluster: int = 0, handoff: int = 0):
+    def __init__(self, mats, k, p=None, seed: int = 0, cluster: int = 0, handoff: int = 0, order: int = 0):
         keep = []
         nb = len(mats)
         arr = (SvdscMatrix * nb)(*[_csr_struct(a, keep) for a in mats])
         self.k = np.ascontiguousarray(k, dtype=np.int32)
         self.p = np.ascontiguousarray(p if p is not None else self.k, dtype=np.int32)
         self.shapes = [(int(a.m), int(a.n)) for a in mats]
-        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0, 0, 0, handoff)
+        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0, 0, 0, handoff, order)
         self.handle = C.c_void_p()
         _check(lib().svdsc_batch_create(C.byref(self.handle), nb, arr, _ptr(self.k), _ptr(self.p),
                                         C.byref(opt), None), "svdsc_batch_create")

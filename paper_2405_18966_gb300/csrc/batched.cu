@@ -1053,7 +1053,9 @@ struct svdsc_batch {
     BMat *d_mats = nullptr;
     BStat *d_stats = nullptr;
     BParams *d_prm = nullptr;
-    int *d_order = nullptr;      // matrix ids, largest estimated cost first
+    int *d_order = nullptr;      // matrix ids, largest (estimated or measured) cost first
+    std::vector<int> order;      // host copy of the queue order
+    bool reorder = true;         // after a solve, order the queue by the measured cycles
     BQueue *d_q = nullptr;       // queue positions and hand-off counters
     int64_t tstride = 0;
     BLaunch L;                   // the first launch (all matrices)
@@ -1270,6 +1272,8 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     if (Cfix != 0 && Cfix != 1 && Cfix != 2 && Cfix != 4 && Cfix != 8) return SVDSC_ERR_ARG;
     const int Hopt = opt ? opt->batch_handoff : 0;
     if (Hopt < -1) return SVDSC_ERR_ARG;
+    const int Oopt = opt ? opt->batch_order : 0;
+    if (Oopt != 0 && Oopt != 1) return SVDSC_ERR_ARG;
     svdsc_batch *B = new (std::nothrow) svdsc_batch();
     if (!B) return SVDSC_ERR_NOMEM;
     B->nb = nb;
@@ -1319,9 +1323,11 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
         const BMat &M = B->hm[b];
         return (double)(M.m + M.n) * M.t * M.t + 4.0 * (double)M.nnz * M.t;
     };
-    std::vector<int> order(nb);
+    std::vector<int> &order = B->order;
+    order.resize(nb);
     for (int b = 0; b < nb; b++) order[b] = b;
     std::sort(order.begin(), order.end(), [&](int x, int y) { return est_cost(x) > est_cost(y); });
+    B->reorder = Oopt == 0;
     double total = 0.0, worst = 0.0;
     for (int b = 0; b < nb; b++) { total += est_cost(b); worst = std::max(worst, est_cost(b)); }
     // Cluster size: the smallest power of two <= 8 for which the costliest
@@ -1501,6 +1507,20 @@ int svdsc_batch_solve(svdsc_batch *B, double tol, int maxit, double *const *S, d
         }
         if (st[b].err) worst = st[b].err;
         else if (!st[b].converged && worst == SVDSC_OK) worst = SVDSC_NOT_CONVERGED;
+    }
+    if (B->reorder) {
+        // The next solve of this batch takes the matrices in the order of the
+        // cycles they took in this one (largest first, ties by index): a
+        // matrix's cost is mostly its restart count, which no estimate made
+        // before the first solve predicts, so the slowest start first.
+        std::vector<int> &order = B->order;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return st[x].cycles_total != st[y].cycles_total ? st[x].cycles_total > st[y].cycles_total : x < y;
+        });
+        if (cudaMemcpyAsync(B->d_order, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, B->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(B->stream) != cudaSuccess)
+            return SVDSC_ERR_CUDA;
     }
     return worst;
 }

@@ -142,6 +142,26 @@ def test_batched_graph_replay_is_deterministic_and_device_outputs(pkg):
     b.close()
 
 
+def test_batched_queue_order_from_measured_cycles(pkg):
+    """Repeated solves of one batch: the queue follows the previous solve's
+    measured cycles (order=0) or the size estimate (order=1); with one cluster
+    size and no hand-off the results are the same either way, bit for bit."""
+    items = synth.workload_batch(count=8, size_scale=0.05, seed=13)
+    mats, ks = [it.a for it in items], [it.k for it in items]
+    b0 = pkg.Batch(mats, ks, seed=5, cluster=2, handoff=-1, order=0)
+    b1 = pkg.Batch(mats, ks, seed=5, cluster=2, handoff=-1, order=1)
+    runs = [b0.solve(1e-10, 200) for _ in range(3)] + [b1.solve(1e-10, 200)]
+    for r in runs[1:]:
+        for i in range(len(items)):
+            np.testing.assert_array_equal(r["S"][i], runs[0]["S"][i])
+            np.testing.assert_array_equal(r["U"][i], runs[0]["U"][i])
+            assert r["infos"][i]["restarts"] == runs[0]["infos"][i]["restarts"]
+    b0.close()
+    b1.close()
+    with pytest.raises(pkg.SvdscError):
+        pkg.Batch(mats, ks, order=2)
+
+
 def test_batched_limits(pkg):
     a = synth.csr_uniform_rows(500, 400, 5, 10, 1)
     with pytest.raises(pkg.SvdscError) as e:
