@@ -512,7 +512,7 @@ def batch_bytes(info, m, n, nnz, k):
     return tot + info["restarts"] * per_restart
 
 
-def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, plain_sample=8, order=0):
+def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, plain_sample=8, order=0, lead=0):
     """Times the batched form on the synthetic batch (device outputs, the
     graph replayed), with the per-cluster balance, the hand-off and the plain
     FP64 form on a sample.  Returns (result dict, items, last outputs, batch)."""
@@ -523,7 +523,7 @@ def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, pla
     mats = [it.a for it in items]
     ks = [it.k for it in items]
     t0 = time.perf_counter()
-    b = pkg.Batch(mats, ks, ks, seed=1, cluster=cluster, handoff=handoff, order=order)
+    b = pkg.Batch(mats, ks, ks, seed=1, cluster=cluster, handoff=handoff, order=order, lead=lead)
     create_s = time.perf_counter() - t0
     first_s = None
     for w_i in range(warmup):
@@ -588,14 +588,14 @@ def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, pla
     peaks, src = load_peaks()
     gbs = tot_bytes / wall / 1e9
     res = {"value": wall, "unit": "s", "steps": steps, "warmup": warmup, "clocks": clocks,
-           "gpu_launches": (2 if hand["idle_threshold"] > 0 else 1) * steps,
+           "gpu_launches": ((2 if hand["idle_threshold"] > 0 else 1) + (1 if b.lead()["clusters"] else 0)) * steps,
            "config": {"workload": f"batch of {count} CSR matrices (m 2k-60k, n 1k-30k, 5-50 nnz/row, FP32, "
                                   f"k 5-40, p = k), one persistent launch per solve (two with the hand-off)",
                       "scale": scale, "matrices": count, "total_nnz": int(sum(a.nnz for a in mats)),
                       "l2": "inputs larger than L2 (no flush)"},
            "batch": {"converged": nconv, "restarts_mean": float(np.mean(rs)),
                      "create_s": create_s, "generate_s": gen_s, "tuning": b.tuning(0), "layout": lay,
-                     "handoff": hand,
+                     "handoff": hand, "lead": b.lead(),
                      "queue_order": "cycles each matrix took in the previous solve of the batch (largest "
                                     "first); the first solve, by the size estimate, took first_solve_s",
                      "first_solve_s": first_s,
@@ -613,7 +613,7 @@ def run_batch(args, ws, rank):
     _build.build()
     count = max(1, int(round(256 * args.batch_frac)))
     res, items, out, b = measure_batch(pkg, torch, count, args.scale, args.batch_cluster, args.batch_handoff,
-                                       args.warmup, args.steps, order=args.batch_order)
+                                       args.warmup, args.steps, order=args.batch_order, lead=args.batch_lead)
     per_triplet = None
     if not args.no_per_triplet:
         idx = batch_sample_indices(count) if (count == 256 and args.scale == 1.0) else [0]
@@ -726,6 +726,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch-frac", type=float, default=1.0, help="fraction of the 256-matrix batch")
     ap.add_argument("--batch-cluster", type=int, default=0, help="CTAs per matrix (0: automatic)")
+    ap.add_argument("--batch-lead", type=int, default=0,
+                    help="lead clusters of 8 CTAs beside the main launch: 0 automatic, -1 none, n > 0")
     ap.add_argument("--batch-order", type=int, default=0,
                     help="batch queue order: 0 the previous solve's measured cycles, 1 the size estimate")
     ap.add_argument("--batch-handoff", type=int, default=0,

@@ -132,6 +132,8 @@ typedef struct svdsc_options {
     int32_t batch_order;   /* batched form, queue order: 0 = estimated cost for the first solve, then
                               the cycles each matrix took in the previous solve of the batch; 1 =
                               the estimate always */
+    int32_t batch_lead;    /* batched form, lead clusters of 8 CTAs beside smaller ones: 0 automatic,
+                              -1 none, n > 0 (see svdsc_batch_lead) */
 } svdsc_options;
 
 /* Kernel categories of svdsc_info.ms / launches / bytes / flops. */
@@ -383,6 +385,17 @@ int svdsc_batch_layout(const svdsc_batch *b, int *cluster_size, int *clusters);
  * the second launch in svdsc_batch_profile. */
 int svdsc_batch_handoff(const svdsc_batch *b, int *idle_threshold, int *cluster_size, int *clusters,
                         int *handed_off);
+
+/* The lead launch (each output may be NULL): its cluster size (8) and
+ * cluster count (0: none).  When the main launch's clusters are smaller than
+ * 8 CTAs, a lead launch of a few 8-CTA clusters starts first; the main launch
+ * follows as soon as every lead CTA runs (programmatic dependent launch) and
+ * gives up the SMs they hold.  Lead cluster i takes queue position i (the
+ * costliest matrices), then shares the queue; lead clusters never hand off.
+ * Automatic (options.batch_lead = 0): two, when the batch has more matrices
+ * than the main launch has clusters.  A matrix solved by a lead cluster
+ * reports cluster 200000 + its lead cluster in svdsc_batch_profile. */
+int svdsc_batch_lead(const svdsc_batch *b, int *cluster_size, int *clusters);
 
 /* Per-matrix profile of the last batch solve (arrays of nb entries, each may
  * be NULL): SM clock cycles of the whole solve, of the projected SVDs and of

@@ -34,7 +34,7 @@ EXPORTS = ("svdsc_create", "svdsc_solve", "svdsc_destroy", "svdsc_strerror", "sv
            "svdsc_cgs2", "svdsc_small_svd", "svdsc_reserve", "svdsc_cgs2_noalloc",
            "svdsc_gemm", "svdsc_batch_create", "svdsc_batch_solve", "svdsc_batch_tuning",
            "svdsc_batch_destroy", "svdsc_solve_batched", "svdsc_batch_layout", "svdsc_batch_profile",
-           "svdsc_batch_phase_cycles", "svdsc_batch_handoff",
+           "svdsc_batch_phase_cycles", "svdsc_batch_handoff", "svdsc_batch_lead",
            "svdsc_selftest_wait")
 
 
@@ -50,7 +50,7 @@ class SvdscOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("timing", C.c_int32), ("seed", C.c_uint64),
                 ("restart_gemm", C.c_int32), ("batch_cluster", C.c_int32), ("which", C.c_int32),
                 ("reorth", C.c_int32), ("block", C.c_int32), ("batch_handoff", C.c_int32),
-                ("batch_order", C.c_int32)]
+                ("batch_order", C.c_int32), ("batch_lead", C.c_int32)]
 
 
 NUM_PHASES = 8
@@ -108,6 +108,7 @@ def lib():
         L.svdsc_batch_profile.argtypes = [vp, vp, vp, vp, vp]
         L.svdsc_batch_phase_cycles.argtypes = [vp, vp]
         L.svdsc_batch_handoff.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.svdsc_batch_lead.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.svdsc_selftest_wait.argtypes = [vp, i32]
         L.svdsc_solve_batched.argtypes = [i32, C.POINTER(SvdscMatrix), vp, vp, dbl, i32, vp, vp, vp, vp,
                                           i32, C.POINTER(SvdscOptions), C.POINTER(SvdscInfo)]
@@ -332,16 +333,18 @@ class Batch:
     handoff: 0 automatic, -1 never, h > 0 hand the running matrices to a second
     launch of 8-CTA clusters once h clusters of the first are idle.
     order: 0 queue by the previous solve's measured cycles (the size estimate
-    for the first solve), 1 by the estimate always."""
+    for the first solve), 1 by the estimate always.
+    lead: 0 automatic, -1 none, n > 0 lead clusters of 8 CTAs beside the main launch."""
 
-    def __init__(self, mats, k, p=None, seed: int = 0, cluster: int = 0, handoff: int = 0, order: int = 0):
+    def __init__(self, mats, k, p=None, seed: int = 0, cluster: int = 0, handoff: int = 0, order: int = 0,
+                 lead: int = 0):
         keep = []
         nb = len(mats)
         arr = (SvdscMatrix * nb)(*[_csr_struct(a, keep) for a in mats])
         self.k = np.ascontiguousarray(k, dtype=np.int32)
         self.p = np.ascontiguousarray(p if p is not None else self.k, dtype=np.int32)
         self.shapes = [(int(a.m), int(a.n)) for a in mats]
-        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0, 0, 0, handoff, order)
+        opt = SvdscOptions(MIXED, 0, seed, 0, cluster, 0, 0, 0, handoff, order, lead)
         self.handle = C.c_void_p()
         _check(lib().svdsc_batch_create(C.byref(self.handle), nb, arr, _ptr(self.k), _ptr(self.p),
                                         C.byref(opt), None), "svdsc_batch_create")
@@ -349,6 +352,12 @@ class Batch:
     def layout(self):
         a, b = C.c_int(), C.c_int()
         _check(lib().svdsc_batch_layout(self.handle, C.byref(a), C.byref(b)), "svdsc_batch_layout")
+        return {"cluster_size": a.value, "clusters": b.value}
+
+    def lead(self):
+        """The lead launch: cluster size and cluster count (0: none)."""
+        a, b = C.c_int(), C.c_int()
+        _check(lib().svdsc_batch_lead(self.handle, C.byref(a), C.byref(b)), "svdsc_batch_lead")
         return {"cluster_size": a.value, "clusters": b.value}
 
     def handoff(self):

@@ -794,11 +794,11 @@ __device__ void solve_one(const BMat &M, int b, BStat *st, const BSlot &slot, do
     const long long c_start = clock64();
     long long c_svd = 0, c_lbp = 0;
     int restarts = 0, it0 = 1;
-    if (mode == 0) {
+    if (mode != 1) {
         if (threadIdx.x == 0 && R.lead) {
             st->converged = 0; st->nconv = 0; st->restarts = 0; st->breakdowns = 0;
             st->n_matvec = 0; st->n_steps = 0; st->err = 0; st->svd_sweeps = 0;
-            st->cluster = (int)cl_id();
+            st->cluster = (mode == 2 ? 200000 : 0) + (int)cl_id();
             for (int q2 = 0; q2 < 5; q2++) st->cycles_phase[q2] = 0;
         }
         for (int64_t i = threadIdx.x; i < (int64_t)(t + 1) * (t + 1); i += kBT) R.T[i] = 0.0;
@@ -964,9 +964,13 @@ __device__ void solve_one(const BMat &M, int b, BStat *st, const BSlot &slot, do
 }
 
 // The persistent kernel.  mode 0 takes matrices from the queue order[0..n),
-// largest estimated cost first; a cluster that finds it empty counts itself
-// idle and leaves.  mode 1 (the second launch, larger clusters) resumes the
-// matrices the first launch handed off.
+// largest cost first; a cluster that finds it empty counts itself idle and
+// leaves.  mode 1 (the second launch, larger clusters) resumes the matrices
+// the first launch handed off.  mode 2 (the lead launch: a few larger
+// clusters running beside mode 0) takes queue position cl_id() first, the
+// costliest matrices, then shares the queue with mode 0; it never hands off
+// and is not counted as idle.  A lead launch lets the launch that follows it
+// in the stream start as soon as every one of its CTAs is running.
 __global__ void __launch_bounds__(kBT, 1)
 batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, int n, BQueue *q, int *ho_list,
                int mode, BStat *stats, const BSlot *__restrict__ slots, double *Tall, int64_t tstride,
@@ -979,16 +983,18 @@ batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, int
     const BSlot slot = slots[cl_id()];
     double *Tpriv = Tall + (int64_t)blockIdx.x * tstride;
     const BParams P = *prm;
+    if (mode == 2) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     int phase = 0;
+    bool reserved = mode == 2;
     while (true) {
         __syncthreads();
         cl_sync();  // every CTA has read the previous item
         if (threadIdx.x == 0 && cl_rank() == 0) {
             int b = -1;
-            if (mode == 0) {
-                const int i = atomicAdd(&q->next, 1);
+            if (mode != 1) {
+                const int i = reserved ? (int)cl_id() : atomicAdd(&q->next, 1);
                 if (i < n) b = order[i];
-                else atomicAdd(&q->idle, 1);
+                else if (mode == 0) atomicAdd(&q->idle, 1);
             } else {
                 const int i = atomicAdd(&q->next2, 1);
                 if (i < *(volatile int *)&q->ho_count) b = ho_list[i];
@@ -1000,6 +1006,7 @@ batched_kernel(const BMat *__restrict__ mats, const int *__restrict__ order, int
         const int b = cl_ld_i32(&item, 0);
         cl_sync();  // no CTA leaves while another still reads its shared memory
         if (b < 0) break;
+        reserved = false;
         solve_one(mats[b], b, stats + b, slot, Tpriv, P, sm, smf, phase, mode, q, ho_list);
     }
 }
@@ -1060,7 +1067,9 @@ struct svdsc_batch {
     int64_t tstride = 0;
     BLaunch L;                   // the first launch (all matrices)
     BLaunch L2;                  // the second launch (matrices handed off), csize 0 when off
+    BLaunch LA;                  // the lead launch beside L (8-CTA clusters), nslots 0 when off
     int handoff_idle = 0;        // hand off once this many clusters of L are idle (0: never)
+    BQueue *h_q0 = nullptr;      // pinned: the queue state each solve starts from
     int *d_ho = nullptr;         // hand-off list (nb entries)
     double *ckv_mem = nullptr;   // v_{k+1} of each matrix (sum of n)
     BHand *d_hand = nullptr;     // nb entries
@@ -1174,6 +1183,7 @@ int svdsc_batch_destroy(svdsc_batch *B)
     if (B->graph) cudaGraphDestroy(B->graph);
     cudaFreeHost(B->h_mats);
     cudaFreeHost(B->h_prm);
+    cudaFreeHost(B->h_q0);
     cudaFree(B->d_mats);
     cudaFree(B->d_stats);
     cudaFree(B->d_prm);
@@ -1183,6 +1193,7 @@ int svdsc_batch_destroy(svdsc_batch *B)
     cudaFree(B->ckv_mem);
     cudaFree(B->d_hand);
     free_launch(B->L2);  // may alias L's memory: freed first, without it
+    free_launch(B->LA);
     free_launch(B->L);
     cudaFree(B->out_mem);
     if (B->stream) cudaStreamDestroy(B->stream);
@@ -1274,6 +1285,8 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     if (Hopt < -1) return SVDSC_ERR_ARG;
     const int Oopt = opt ? opt->batch_order : 0;
     if (Oopt != 0 && Oopt != 1) return SVDSC_ERR_ARG;
+    const int Aopt = opt ? opt->batch_lead : 0;
+    if (Aopt < -1) return SVDSC_ERR_ARG;
     svdsc_batch *B = new (std::nothrow) svdsc_batch();
     if (!B) return SVDSC_ERR_NOMEM;
     B->nb = nb;
@@ -1345,6 +1358,26 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     if (cap < 1) { svdsc_batch_destroy(B); return SVDSC_ERR_CUDA; }
     B->L.csize = C;
     B->L.nslots = std::min(nb, cap);
+    // Lead launch: a few 8-CTA clusters that start before the main launch
+    // and take the first queue positions, the costliest matrices (by the
+    // previous solve's cycles once there is one), which scale almost linearly
+    // from 4 to 8 CTAs and would otherwise be the batch's critical path on
+    // the main launch's smaller clusters.  Automatic: two, when the batch is
+    // longer than one wave of the main launch's clusters.  The main launch
+    // gives up the SMs the lead clusters hold.
+    if (C < 8 && Aopt >= 0) {
+        const int cap8 = max_clusters(8);
+        int nlead = Aopt > 0 ? std::min(Aopt, cap8) : ((nb > cap && cap8 >= 2) ? 2 : 0);
+        nlead = std::min(nlead, nb);
+        const int displaced = (nlead * 8 + C - 1) / C;
+        if (nlead > 0 && cap - displaced >= 1) {
+            B->L.nslots = std::min(B->L.nslots, cap - displaced);
+            B->LA.csize = 8;
+            B->LA.nslots = nlead;
+            rc = setup_launch(B, B->LA, mmax, nmax, tmax);
+            if (rc) { svdsc_batch_destroy(B); return rc; }
+        }
+    }
     rc = setup_launch(B, B->L, mmax, nmax, tmax);
     if (rc) { svdsc_batch_destroy(B); return rc; }
     // Hand-off: once the queue is empty and enough clusters are idle, the
@@ -1373,7 +1406,12 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
               cudaMalloc(&B->d_prm, sizeof(BParams)) == cudaSuccess &&
               cudaMalloc(&B->d_q, sizeof(BQueue)) == cudaSuccess &&
               cudaMallocHost(&B->h_mats, sizeof(BMat) * nb) == cudaSuccess &&
-              cudaMallocHost(&B->h_prm, sizeof(BParams)) == cudaSuccess;
+              cudaMallocHost(&B->h_prm, sizeof(BParams)) == cudaSuccess &&
+              cudaMallocHost(&B->h_q0, sizeof(BQueue)) == cudaSuccess;
+    if (ok) {
+        memset(B->h_q0, 0, sizeof(BQueue));
+        B->h_q0->next = B->LA.nslots;  // the lead clusters hold positions [0, nslots)
+    }
     if (ok && B->handoff_idle > 0)
         ok = cudaMalloc(&B->d_ho, sizeof(int) * nb) == cudaSuccess &&
              cudaMalloc(&B->ckv_mem, sizeof(double) * ntot) == cudaSuccess &&
@@ -1424,10 +1462,14 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     return SVDSC_OK;
 }
 
-static cudaError_t launch_batched(svdsc_batch *B, const BLaunch &L, int mode, cudaStream_t s)
+static cudaError_t launch_batched(svdsc_batch *B, const BLaunch &L, int mode, cudaStream_t s, bool after_lead = false)
 {
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
+    // after the lead launch: start once every lead CTA runs (they signal it
+    // at their start), not when the lead launch ends
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = L.csize;
     at[0].val.clusterDim.y = 1;
@@ -1437,7 +1479,7 @@ static cudaError_t launch_batched(svdsc_batch *B, const BLaunch &L, int mode, cu
     cfg.dynamicSmemBytes = kSmBytes;
     cfg.stream = s;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = after_lead ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, batched_kernel, (const BMat *)B->d_mats, (const int *)B->d_order, B->nb,
                               B->d_q, B->d_ho, mode, B->d_stats, (const BSlot *)L.d_slots, L.d_T, B->tstride,
                               (const BParams *)B->d_prm);
@@ -1467,9 +1509,11 @@ int svdsc_batch_solve(svdsc_batch *B, double tol, int maxit, double *const *S, d
         if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SVDSC_ERR_CUDA;
         cudaMemcpyAsync(B->d_mats, B->h_mats, sizeof(BMat) * nb, cudaMemcpyHostToDevice, B->stream);
         cudaMemcpyAsync(B->d_prm, B->h_prm, sizeof(BParams), cudaMemcpyHostToDevice, B->stream);
-        cudaMemsetAsync(B->d_q, 0, sizeof(BQueue), B->stream);
+        cudaMemcpyAsync(B->d_q, B->h_q0, sizeof(BQueue), cudaMemcpyHostToDevice, B->stream);
         cudaMemsetAsync(B->d_stats, 0, sizeof(BStat) * nb, B->stream);
-        cudaError_t e = launch_batched(B, B->L, 0, B->stream);
+        cudaError_t e = cudaSuccess;
+        if (B->LA.nslots > 0) e = launch_batched(B, B->LA, 2, B->stream);
+        if (e == cudaSuccess) e = launch_batched(B, B->L, 0, B->stream, B->LA.nslots > 0);
         if (e == cudaSuccess && B->handoff_idle > 0) e = launch_batched(B, B->L2, 1, B->stream);
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(B->stream, &g);
@@ -1579,6 +1623,14 @@ int svdsc_batch_layout(const svdsc_batch *B, int *cluster_size, int *clusters)
     if (!B) return SVDSC_ERR_ARG;
     if (cluster_size) *cluster_size = B->L.csize;
     if (clusters) *clusters = B->L.nslots;
+    return SVDSC_OK;
+}
+
+int svdsc_batch_lead(const svdsc_batch *B, int *cluster_size, int *clusters)
+{
+    if (!B) return SVDSC_ERR_ARG;
+    if (cluster_size) *cluster_size = B->LA.csize;
+    if (clusters) *clusters = B->LA.nslots;
     return SVDSC_OK;
 }
 

@@ -121,6 +121,30 @@ def test_batched_handoff_vs_oracle(pkg, orc, cluster):
     b.close()
 
 
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_batched_lead_clusters_vs_oracle(pkg, orc, cluster):
+    """A lead launch of one 8-CTA cluster beside clusters of 1 or 2 CTAs (and
+    the hand-off after them): the lead cluster takes the first queue position
+    and then shares the queue; every result against the oracle, twice (the
+    second solve queued by the first one's cycles)."""
+    items = synth.workload_batch(count=10, size_scale=0.08, seed=7)
+    b = pkg.Batch([it.a for it in items], [it.k for it in items], [it.k for it in items], seed=3,
+                  cluster=cluster, handoff=1, lead=1)
+    assert b.lead() == {"cluster_size": 8, "clusters": 1}
+    for rep in range(2):
+        out = b.solve(1e-10, 200)
+        cl = b.profile()["cluster"]
+        assert int(np.sum(cl >= 200000)) >= 1
+        for i, it in enumerate(items):
+            info = out["infos"][i]
+            assert info["err"] == 0 and info["converged"] == 1, (i, info)
+            check_vs_oracle(orc, it.a, it.k, out["S"][i], out["U"][i], out["V"][i], maxit=200)
+            assert info["n_matvec"] == 2 * info["t"] + 2 * info["restarts"] * (info["t"] - it.k)
+    b.close()
+    with pytest.raises(pkg.SvdscError):
+        pkg.Batch([it.a for it in items], [it.k for it in items], lead=-2)
+
+
 def test_batched_handoff_off(pkg):
     items = synth.workload_batch(count=4, size_scale=0.05, seed=11)
     b = pkg.Batch([it.a for it in items], [it.k for it in items], seed=5, cluster=1, handoff=-1)
