@@ -590,7 +590,7 @@ def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, pla
     res = {"value": wall, "unit": "s", "steps": steps, "warmup": warmup, "clocks": clocks,
            "gpu_launches": ((2 if hand["idle_threshold"] > 0 else 1) + (1 if b.lead()["clusters"] else 0)) * steps,
            "config": {"workload": f"batch of {count} CSR matrices (m 2k-60k, n 1k-30k, 5-50 nnz/row, FP32, "
-                                  f"k 5-40, p = k), one persistent launch per solve (two with the hand-off)",
+                                  f"k 5-40, p = k), persistent launches per solve: lead, main, hand-off",
                       "scale": scale, "matrices": count, "total_nnz": int(sum(a.nnz for a in mats)),
                       "l2": "inputs larger than L2 (no flush)"},
            "batch": {"converged": nconv, "restarts_mean": float(np.mean(rs)),

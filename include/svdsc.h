@@ -327,7 +327,8 @@ int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, int64_t ldw,
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent truncated SVDs (uneven shapes and k) solved
- * in one persistent kernel launch (two with the hand-off), replayed from a
+ * in one persistent kernel launch (plus a lead launch and a hand-off launch
+ * when they are on), replayed from a
  * CUDA graph.  Thread-block clusters (1-8 CTAs) take matrices from a work
  * queue (largest cost first: estimated from the sizes for the first solve,
  * then, unless options.batch_order = 1, the cycles each matrix took in the
@@ -392,7 +393,7 @@ int svdsc_batch_handoff(const svdsc_batch *b, int *idle_threshold, int *cluster_
  * follows as soon as every lead CTA runs (programmatic dependent launch) and
  * gives up the SMs they hold.  Lead cluster i takes queue position i (the
  * costliest matrices), then shares the queue; lead clusters never hand off.
- * Automatic (options.batch_lead = 0): two, when the batch has more matrices
+ * Automatic (options.batch_lead = 0): one, when the batch has more matrices
  * than the main launch has clusters.  A matrix solved by a lead cluster
  * reports cluster 200000 + its lead cluster in svdsc_batch_profile. */
 int svdsc_batch_lead(const svdsc_batch *b, int *cluster_size, int *clusters);

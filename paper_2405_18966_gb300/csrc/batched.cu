@@ -1362,12 +1362,13 @@ int svdsc_batch_create(svdsc_batch **out, int nb, const svdsc_matrix *As, const 
     // and take the first queue positions, the costliest matrices (by the
     // previous solve's cycles once there is one), which scale almost linearly
     // from 4 to 8 CTAs and would otherwise be the batch's critical path on
-    // the main launch's smaller clusters.  Automatic: two, when the batch is
-    // longer than one wave of the main launch's clusters.  The main launch
-    // gives up the SMs the lead clusters hold.
+    // the main launch's smaller clusters.  Automatic: one (1, 2, 3 and 4
+    // measured within 3 % of each other on the 256-matrix batch, one best),
+    // when the batch is longer than one wave of the main launch's clusters.
+    // The main launch gives up the SMs the lead clusters hold.
     if (C < 8 && Aopt >= 0) {
         const int cap8 = max_clusters(8);
-        int nlead = Aopt > 0 ? std::min(Aopt, cap8) : ((nb > cap && cap8 >= 2) ? 2 : 0);
+        int nlead = Aopt > 0 ? std::min(Aopt, cap8) : ((nb > cap && cap8 >= 2) ? 1 : 0);
         nlead = std::min(nlead, nb);
         const int displaced = (nlead * 8 + C - 1) / C;
         if (nlead > 0 && cap - displaced >= 1) {
