@@ -196,19 +196,31 @@ __device__ void cta_spmv_g(const int64_t *__restrict__ rp, const int32_t *__rest
 {
     const int grp = threadIdx.x / G, lg = threadIdx.x % G;
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    for (int64_t r = grp; r < rows; r += kBT / G) {
-        const int64_t e0 = rp[r], e1 = rp[r + 1];
-        float a0 = 0.f, a1 = 0.f;
+    constexpr int64_t kStep = kBT / G;
+    // the next row's extent is loaded while this row is summed, so a row costs
+    // one dependent memory latency (the matrix entries) instead of two
+    int64_t e0n = 0, e1n = 0;
+    if (grp < rows) { e0n = rp[grp]; e1n = rp[grp + 1]; }
+    for (int64_t r = grp; r < rows; r += kStep) {
+        const int64_t e0 = e0n, e1 = e1n;
+        if (r + kStep < rows) { e0n = rp[r + kStep]; e1n = rp[r + kStep + 1]; }
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
         int64_t e = e0 + lg;
-        // the matrix streams with evict-first loads; x was written earlier in this
-        // launch by the cluster's CTAs, so it is read with ordinary (coherent)
-        // loads, never through the read-only path
-        for (; e + G < e1; e += 2 * G) {
-            a0 = fmaf(__ldcs(val + e), x[__ldcs(col + e)], a0);
-            a1 = fmaf(__ldcs(val + e + G), x[__ldcs(col + e + G)], a1);
+        // the matrix streams with evict-first loads, four entries in flight per
+        // lane; x was written earlier in this launch by the cluster's CTAs, so it
+        // is read with ordinary (coherent) loads, never through the read-only path
+        for (; e + 3 * G < e1; e += 4 * G) {
+            const int32_t c0 = __ldcs(col + e), c1 = __ldcs(col + e + G);
+            const int32_t c2 = __ldcs(col + e + 2 * G), c3 = __ldcs(col + e + 3 * G);
+            const float v0 = __ldcs(val + e), v1 = __ldcs(val + e + G);
+            const float v2 = __ldcs(val + e + 2 * G), v3 = __ldcs(val + e + 3 * G);
+            a0 = fmaf(v0, x[c0], a0);
+            a1 = fmaf(v1, x[c1], a1);
+            a2 = fmaf(v2, x[c2], a2);
+            a3 = fmaf(v3, x[c3], a3);
         }
-        if (e < e1) a0 = fmaf(__ldcs(val + e), x[__ldcs(col + e)], a0);
-        float s = a0 + a1;
+        for (; e < e1; e += G) a0 = fmaf(__ldcs(val + e), x[__ldcs(col + e)], a0);
+        float s = (a0 + a1) + (a2 + a3);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
         if (lg == 0) y[r] = (double)s - (z ? coef * z[r] : 0.0);
