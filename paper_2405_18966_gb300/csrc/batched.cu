@@ -167,7 +167,7 @@ constexpr int kSmSig = kSmRed + 4 * kBW;              // unsorted sigma (t)
 constexpr int kSmPart = kSmSig + kBMaxT;               // cluster partials: 2 x (t + 8)
 constexpr int kSmRowPart = kSmPart + 2 * (kBMaxT + 8);  // projection partials: 8 x (t + 8)
 constexpr int kSmDoubles = kSmRowPart + 8 * (kBMaxT + 8);
-// floats after the doubles: Q_U (t x k), Q_V (t x k), h32 (t + 2)
+// floats after the doubles: Q_U (t x k, row c at Q + c kBMaxK), Q_V (the same), h32 (t + 2)
 constexpr int kSmQU = 0;
 constexpr int kSmQV = kSmQU + kBMaxT * kBMaxK;
 constexpr int kSmH32 = kSmQV + kBMaxT * kBMaxK;
@@ -636,37 +636,58 @@ __device__ void cta_small_svd(BRun &R)
         }
         if (rank < k)
             for (int r = lane; r < t; r += 32) {
-                QU[r + rank * t] = sj > 0.0 ? (float)(B[r + j * t] / sj) : 0.f;
-                QV[r + rank * t] = (float)Wm[r + j * t];
+                QU[rank + r * kBMaxK] = sj > 0.0 ? (float)(B[r + j * t] / sj) : 0.f;
+                QV[rank + r * kBMaxK] = (float)Wm[r + j * t];
             }
     }
     __syncthreads();
     if (threadIdx.x == 0 && R.lead) R.st->svd_sweeps = conv ? sweeps : -1;
 }
 
-// C (rows x k) = W32 (rows x t) Q (t x k, FP32 in shared memory), FP32 FMA;
-// C in FP64 (and its FP32 shadow when C32 != null).
-__device__ void cta_gemm32(const float *__restrict__ W32, int64_t ld, int64_t rows, int t, const float *Q, int k,
-                           double *__restrict__ C, float *__restrict__ C32, int64_t ldc)
+// C (rows x k) = W32 (rows x t) Q (t x k, FP32 in shared memory, row c of Q
+// at Q + c kBMaxK), FP32 FMA, each output summed over c in order; C in FP64
+// (and its FP32 shadow when C32 != null).  KB (k rounded up to 16) accumulators
+// per row; a row of Q is read as float4, and the next W entry is loaded while
+// the current one is used.
+template <int KB>
+__device__ void cta_gemm32_k(const float *__restrict__ W32, int64_t ld, int64_t rows, int t, const float *Q,
+                             int k, double *__restrict__ C, float *__restrict__ C32, int64_t ldc)
 {
     for (int64_t r = threadIdx.x; r < rows; r += kBT) {
-        float acc[kBMaxK];
+        float acc[KB];
 #pragma unroll
-        for (int j = 0; j < kBMaxK; j++) acc[j] = 0.f;
+        for (int j = 0; j < KB; j++) acc[j] = 0.f;
+        float a_next = t > 0 ? W32[r] : 0.f;
         for (int c = 0; c < t; c++) {
-            const float a = W32[r + (int64_t)c * ld];
+            const float a = a_next;
+            if (c + 1 < t) a_next = W32[r + (int64_t)(c + 1) * ld];
+            const float4 *q = (const float4 *)(Q + c * kBMaxK);
 #pragma unroll
-            for (int j = 0; j < kBMaxK; j++)
-                if (j < k) acc[j] = fmaf(a, Q[c + j * t], acc[j]);
+            for (int jj = 0; jj < KB / 4; jj++) {
+                const float4 qv = q[jj];
+                acc[4 * jj] = fmaf(a, qv.x, acc[4 * jj]);
+                acc[4 * jj + 1] = fmaf(a, qv.y, acc[4 * jj + 1]);
+                acc[4 * jj + 2] = fmaf(a, qv.z, acc[4 * jj + 2]);
+                acc[4 * jj + 3] = fmaf(a, qv.w, acc[4 * jj + 3]);
+            }
         }
 #pragma unroll
-        for (int j = 0; j < kBMaxK; j++)
+        for (int j = 0; j < KB; j++)
             if (j < k) {
                 C[r + (int64_t)j * ldc] = (double)acc[j];
                 if (C32) C32[r + (int64_t)j * ldc] = acc[j];
             }
     }
     __syncthreads();
+}
+
+__device__ void cta_gemm32(const float *__restrict__ W32, int64_t ld, int64_t rows, int t, const float *Q, int k,
+                           double *__restrict__ C, float *__restrict__ C32, int64_t ldc)
+{
+    static_assert(kBMaxK == 48, "accumulator buckets");
+    if (k <= 16) cta_gemm32_k<16>(W32, ld, rows, t, Q, k, C, C32, ldc);
+    else if (k <= 32) cta_gemm32_k<32>(W32, ld, rows, t, Q, k, C, C32, ldc);
+    else cta_gemm32_k<48>(W32, ld, rows, t, Q, k, C, C32, ldc);
 }
 
 // sign rule: v_j's largest-magnitude entry (lowest index on ties) positive;
