@@ -564,7 +564,9 @@ def measure_batch(pkg, torch, count, scale, cluster, handoff, warmup, steps, pla
                "slowest_matrix_s": float(prof["cycles_total"].max() / clk),
                "slowest": [{"m": int(items[i].a.m), "n": int(items[i].a.n), "nnz": int(items[i].a.nnz),
                             "k": int(items[i].k), "restarts": int(infos[i]["restarts"]),
-                            "s": float(prof["cycles_total"][i] / clk), "handed_off": bool(prof["cluster"][i] >= 100000),
+                            "s": float(prof["cycles_total"][i] / clk),
+                            "handed_off": bool(100000 <= prof["cluster"][i] < 200000),
+                            "lead_cluster": bool(prof["cluster"][i] >= 200000),
                             "svd_s": float(prof["cycles_svd"][i] / clk), "lbp_s": float(prof["cycles_lbp"][i] / clk)}
                            for i in np.argsort(-prof["cycles_total"])[:5]]}
     balance["wall_over_ideal"] = wall / balance["ideal_s"]

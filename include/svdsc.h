@@ -130,8 +130,8 @@ typedef struct svdsc_options {
     int32_t batch_handoff; /* batched form, hand-off to a second launch: 0 automatic, -1 never,
                               h > 0 once h clusters of the first launch are idle */
     int32_t batch_order;   /* batched form, queue order: 0 = estimated cost for the first solve, then
-                              the cycles each matrix took in the previous solve of the batch; 1 =
-                              the estimate always */
+                              the SM cycles (cycles x CTAs) each matrix took in the previous solve of
+                              the batch; 1 = the estimate always */
     int32_t batch_lead;    /* batched form, lead clusters of 8 CTAs beside smaller ones: 0 automatic,
                               -1 none, n > 0 (see svdsc_batch_lead) */
 } svdsc_options;
@@ -331,8 +331,8 @@ int svdsc_cgs2_noalloc(int64_t len, int64_t ncols, const double *W, int64_t ldw,
  * when they are on), replayed from a
  * CUDA graph.  Thread-block clusters (1-8 CTAs) take matrices from a work
  * queue (largest cost first: estimated from the sizes for the first solve,
- * then, unless options.batch_order = 1, the cycles each matrix took in the
- * previous solve of the same batch) and run Alg. 2 for each.  Hand-off:
+ * then, unless options.batch_order = 1, the SM cycles each matrix took in
+ * the previous solve of the same batch) and run Alg. 2 for each.  Hand-off:
  * once the queue is empty and a set number of clusters are idle, the matrices
  * still running stop at their next restart boundary (after the restart GEMM
  * of Eq. 6) and a second launch of 8-CTA clusters resumes them from the saved

@@ -56,6 +56,7 @@ struct BHand {
     unsigned long long draws;
     int restarts, it;
     long long cycles_total, cycles_svd, cycles_lbp;
+    long long work;  // cycles x CTAs of the first launch's share
     double S[kBMaxK], rho[kBMaxK];  // the k Ritz values and restart coefficients
 };
 
@@ -75,6 +76,7 @@ struct BStat {
     int64_t cycles_total, cycles_svd, cycles_lbp;  // SM clock cycles on the cluster leader
     int cluster, pad;
     int64_t cycles_phase[5];  // SpMV, FP32 CGS pass, FP64 CGS pass, norm/scale, restart/output GEMM
+    int64_t work;             // SM cycles: cycles on the leader x CTAs of its cluster, summed over launches
 };
 
 struct BSlot {   // one per cluster (bases), T one per CTA
@@ -941,6 +943,7 @@ __device__ void solve_one(const BMat &M, int b, BStat *st, const BSlot &slot, do
                         H->restarts = restarts;
                         H->it = it;
                         H->cycles_total = clock64() - c_start;
+                        H->work = H->cycles_total * (long long)R.csize;
                         H->cycles_svd = c_svd;
                         H->cycles_lbp = c_lbp;
                         for (int q2 = 0; q2 < 5; q2++) st->cycles_phase[q2] = R.cyc[q2];
@@ -983,12 +986,15 @@ __device__ void solve_one(const BMat &M, int b, BStat *st, const BSlot &slot, do
     }
     if (threadIdx.x == 0 && R.lead) {
         long long c_tot = clock64() - c_start;
+        long long work = c_tot * (long long)R.csize;
         if (mode == 1) {  // add the first launch's share
+            work += M.hand->work;
             c_tot += M.hand->cycles_total;
             c_svd += M.hand->cycles_svd;
             c_lbp += M.hand->cycles_lbp;
         }
         st->cycles_total = c_tot;
+        st->work = work;
         st->cycles_svd = c_svd;
         st->cycles_lbp = c_lbp;
         for (int q2 = 0; q2 < 5; q2++) st->cycles_phase[q2] += R.cyc[q2];
@@ -1594,12 +1600,14 @@ int svdsc_batch_solve(svdsc_batch *B, double tol, int maxit, double *const *S, d
     }
     if (B->reorder) {
         // The next solve of this batch takes the matrices in the order of the
-        // cycles they took in this one (largest first, ties by index): a
-        // matrix's cost is mostly its restart count, which no estimate made
-        // before the first solve predicts, so the slowest start first.
+        // SM cycles they took in this one (cycles times the CTAs of the
+        // cluster, so that a matrix that ran on a larger cluster is not
+        // ranked cheaper for it; largest first, ties by index): a matrix's
+        // cost is mostly its restart count, which no estimate made before the
+        // first solve predicts, so the costliest start first.
         std::vector<int> &order = B->order;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-            return st[x].cycles_total != st[y].cycles_total ? st[x].cycles_total > st[y].cycles_total : x < y;
+            return st[x].work != st[y].work ? st[x].work > st[y].work : x < y;
         });
         if (cudaMemcpyAsync(B->d_order, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, B->stream) !=
                 cudaSuccess ||
