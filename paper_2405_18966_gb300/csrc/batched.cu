@@ -565,14 +565,132 @@ __device__ void cta_small_svd(BRun &R)
     constexpr int kLP = 8;  // lanes per column pair (t <= 80: at most 40 pairs, 64 groups)
     const int grp = threadIdx.x / kLP, gl = threadIdx.x % kLP;
     const unsigned gmask = 0xFFu << (lane & ~(kLP - 1));
-    for (int i = threadIdx.x; i < t * t; i += kBT) {
-        const int r = i % t, c = i / t;
-        B[r + c * t] = *Tb(R, r, c);
-        Wm[r + c * t] = (r == c) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    const double tol = DBL_EPSILON * sqrt((double)t);
     const int n2 = t + (t & 1);
+    // FP32 preconditioning: the same round-robin sweeps on an FP32 copy of T
+    // (scaled by a power of two to max |T| < 1) and an FP32 W, both inside B's
+    // region, until every pair is orthogonal to 1e-5 (at most 12 sweeps); the
+    // FP32 pipe has ~64x the FP64 one's rate, and the FP64 sweeps below then
+    // only remove what FP32 cannot resolve (two or three instead of eight or
+    // more).  W is then orthonormalized in FP64 (CGS2) and B = T W is formed
+    // in FP64, so the FP64 sweeps keep the invariant B = T W exactly.
+    {
+        float *B32 = (float *)B, *W32 = (float *)B + t * t;
+        __shared__ unsigned s_exp, s_off;
+        if (threadIdx.x == 0) s_exp = 0u;
+        __syncthreads();
+        unsigned emax = 0u;
+        for (int i = threadIdx.x; i < t * t; i += kBT) {
+            const double x = *Tb(R, i % t, i / t);
+            const unsigned ex = (unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu;
+            if (ex != 0x7FFu && ex > emax) emax = ex;
+        }
+        atomicMax(&s_exp, emax);
+        __syncthreads();
+        const int eb = s_exp == 0u ? 0 : (int)s_exp - 1022;
+        const double scale = ldexp(1.0, -max(-1000, min(1000, eb)));
+        for (int i = threadIdx.x; i < t * t; i += kBT) {
+            const int r = i % t, c = i / t;
+            B32[i] = (float)(*Tb(R, r, c) * scale);
+            W32[i] = (r == c) ? 1.f : 0.f;
+        }
+        __syncthreads();
+        const float tol32 = FLT_EPSILON * sqrtf((float)t);
+        for (int sw = 0; sw < 12; sw++) {
+            if (threadIdx.x == 0) s_off = 0u;
+            __syncthreads();
+            for (int round = 0; round < n2 - 1; round++) {
+                for (int slot = grp; slot < n2 / 2; slot += kBT / kLP) {
+                    auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (n2 - 1)) + 1; };
+                    int p = player(slot), q = player(n2 - 1 - slot);
+                    if (p > q) { const int x = p; p = q; q = x; }
+                    if (q >= t) continue;
+                    float *bp = B32 + p * t, *bq = B32 + q * t;
+                    float a = 0.f, b = 0.f, g = 0.f;
+                    for (int r = gl; r < t; r += kLP) {
+                        const float x = bp[r], y = bq[r];
+                        a = fmaf(x, x, a);
+                        b = fmaf(y, y, b);
+                        g = fmaf(x, y, g);
+                    }
+#pragma unroll
+                    for (int o = kLP / 2; o > 0; o >>= 1) {
+                        a += __shfl_xor_sync(gmask, a, o);
+                        b += __shfl_xor_sync(gmask, b, o);
+                        g += __shfl_xor_sync(gmask, g, o);
+                    }
+                    const float den = sqrtf(a * b);
+                    if (gl == 0 && den > 0.f) {
+                        const float rel = fabsf(g) / den;
+                        if (rel == rel) atomicMax(&s_off, __float_as_uint(rel));
+                    }
+                    if (g == 0.f || !(fabsf(g) > tol32 * den)) continue;
+                    const float d = b - a, g2 = 2.f * g;
+                    const float rr = sqrtf(fmaf(d, d, g2 * g2));
+                    const bool neg = d != 0.f && ((d > 0.f) != (g > 0.f));
+                    const float tn = (neg ? -fabsf(g2) : fabsf(g2)) / (fabsf(d) + rr);
+                    if (!(fabsf(tn) <= 1.f)) continue;  // |tan| <= 1 by construction; drops NaN
+                    const float c = rsqrtf(fmaf(tn, tn, 1.f)), sn = c * tn;
+                    for (int r = gl; r < t; r += kLP) {
+                        const float x = bp[r], y = bq[r];
+                        bp[r] = c * x - sn * y;
+                        bq[r] = sn * x + c * y;
+                    }
+                    float *wp = W32 + p * t, *wq = W32 + q * t;
+                    for (int r = gl; r < t; r += kLP) {
+                        const float x = wp[r], y = wq[r];
+                        wp[r] = c * x - sn * y;
+                        wq[r] = sn * x + c * y;
+                    }
+                }
+                __syncthreads();
+            }
+            const bool stop = __uint_as_float(s_off) < 1e-5f;
+            __syncthreads();  // every thread has read s_off before it is reset
+            if (stop) break;
+        }
+        for (int i = threadIdx.x; i < t * t; i += kBT) Wm[i] = (double)W32[i];
+        __syncthreads();
+        // CGS2 in FP64, column by column: W orthonormal to FP64 precision
+        double *hb = R.sm + kSmH;  // t + 2 doubles, idle during the projected SVD
+        for (int j = 0; j < t; j++) {
+            double *wj = Wm + j * t;
+            for (int pass = 0; pass < 2 && j > 0; pass++) {
+                for (int i = warp; i < j; i += kBW) {
+                    const double *wi = Wm + i * t;
+                    double d = 0.0;
+                    for (int r = lane; r < t; r += 32) d = fma(wi[r], wj[r], d);
+                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                    if (lane == 0) hb[i] = d;
+                }
+                __syncthreads();
+                for (int r = threadIdx.x; r < t; r += kBT) {
+                    double sacc = 0.0;
+                    for (int i = 0; i < j; i++) sacc = fma(hb[i], Wm[r + i * t], sacc);
+                    wj[r] -= sacc;
+                }
+                __syncthreads();
+            }
+            if (warp == 0) {
+                double nn = 0.0;
+                for (int r = lane; r < t; r += 32) nn = fma(wj[r], wj[r], nn);
+                for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+                if (lane == 0) hb[t] = nn;
+            }
+            __syncthreads();
+            const double inv = hb[t] > 0.0 ? 1.0 / sqrt(hb[t]) : 0.0;
+            for (int r = threadIdx.x; r < t; r += kBT) wj[r] *= inv;
+            __syncthreads();
+        }
+        // B = T W (FP64; B32 and W32 are no longer needed)
+        for (int i = threadIdx.x; i < t * t; i += kBT) {
+            const int r = i % t, jc = i / t;
+            double sacc = 0.0;
+            for (int c = 0; c < t; c++) sacc = fma(*Tb(R, r, c), Wm[c + jc * t], sacc);
+            B[r + jc * t] = sacc;
+        }
+        __syncthreads();
+    }
+    const double tol = DBL_EPSILON * sqrt((double)t);
     int sweeps = 0;
     bool conv = false;
     while (sweeps < 100) {
