@@ -124,3 +124,32 @@ def test_noalloc_address_table_is_keyed_by_context(tmp_path):
                     os.path.join(ROOT, "tests", "c", "ctx_cache_test.cpp"), "-o", str(exe)], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and "OK (0 failures)" in r.stdout, r.stdout
+
+
+def test_batched_options_rejected_without_gpu(libpath):
+    """svdsc_batch_create checks its options before any CUDA call: each bad
+    value returns SVDSC_ERR_ARG (and a good set would go on to the device)."""
+    import ctypes as C
+    import numpy as np
+    import paper_2405_18966_gb300 as pkg
+    L = pkg.lib()
+    rp = np.array([0, 1, 2, 3], dtype=np.int64)
+    ci = np.array([0, 1, 2], dtype=np.int32)
+    val = np.ones(3, dtype=np.float32)
+    m = pkg.SvdscMatrix()
+    m.format, m.index_base, m.m, m.n, m.nnz = pkg.CSR_FORMAT, 0, 3, 3, 3
+    m.row_ptr, m.col_idx, m.values = rp.ctypes.data, ci.ctypes.data, val.ctypes.data
+    m.value_type = pkg.F32
+    mats = (pkg.SvdscMatrix * 1)(m)
+    k = np.array([1], dtype=np.int32)
+    p = np.array([1], dtype=np.int32)
+    h = C.c_void_p()
+    bad = [dict(precision=pkg.FP64), dict(batch_cluster=3), dict(batch_handoff=-2), dict(batch_order=2),
+           dict(batch_lead=-2), dict(block=4)]
+    for b in bad:
+        opt = pkg.SvdscOptions(pkg.MIXED, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0)
+        for f, v in b.items():
+            setattr(opt, f, v)
+        rc = L.svdsc_batch_create(C.byref(h), 1, mats, k.ctypes.data_as(C.c_void_p),
+                                  p.ctypes.data_as(C.c_void_p), C.byref(opt), None)
+        assert rc == pkg.ERR_ARG, (b, rc)
